@@ -1,0 +1,160 @@
+/*
+ * dghgks.h -- C ABI of the DG-HGKS per-stage residual on one NVIDIA B300.
+ *
+ * The method is the discontinuous-Galerkin high-order gas-kinetic scheme of
+ * arXiv:2202.13821 for the 3D Euler and Navier-Stokes equations:
+ *   - Sec. 2, Eq. (flux): second-order gas-kinetic interface flux from the
+ *     BGK integral solution, with collision time tau = mu/p (Sec. 3 Remark 1);
+ *   - Sec. 3, Eq. (flux-2): simplified interior flux f = g0(1 - tau(a.u+A) + At);
+ *   - Sec. 3, Eqs. (expansion), (operator), (surface), (volume): P_k Legendre
+ *     modal DG residual R(Q_h), diagonal mass matrix, L = M^-1 R;
+ *   - Sec. 3, Eq. (expansion-1): F and d_t F from the time integrals of the
+ *     flux over [0, dt] and [0, dt/2];
+ *   - Sec. 3, Eq. (two-stage): the two-stage fourth-order (S2O4) step.
+ *
+ * Conventions shared by every call
+ *   State layout: Q[var][mode][z][y][x], float64, contiguous, on the device
+ *   unless the name ends in _host.  var = (rho, rho U, rho V, rho W, rho E)
+ *   with rho E = p/(gamma-1) + rho|U|^2/2.  Modes of P_k by total degree,
+ *   pure powers first: (000) (100)(010)(001) (200)(020)(002)(110)(101)(011).
+ *   Mode n of a cell is the coefficient of P_nx(xi) P_ny(eta) P_nz(zeta) with
+ *   xi = 2 (x - x_i) / dx.  N_m = (k+1)(k+2)(k+3)/6 modes.
+ *   Ownership: the caller owns every state/output buffer.  The library owns
+ *   its scratch (stage buffers, face moments, reduction partials), allocated
+ *   in dghgks_init and freed in dghgks_destroy.
+ *   Streams: `stream` is a cudaStream_t passed as void* (NULL = default
+ *   stream).  Calls enqueue work and return without synchronising, except
+ *   those documented as synchronising.
+ *   Errors: 0 on success, negative otherwise; dghgks_last_error() gives text.
+ *     DGHGKS_EARG    (-1) bad argument (NULL pointer, size, dt <= 0)
+ *     DGHGKS_EUNSUP  (-2) unsupported order / Gauss count / boundary
+ *     DGHGKS_ECUDA   (-3) CUDA error
+ *     DGHGKS_EPHYS   (-4) non-physical state met (rho <= 0 or p <= 0); the
+ *                         kernels set a device flag, read by dghgks_status()
+ *                         and by the synchronising calls; no trap
+ *     DGHGKS_ENOMEM  (-5) device allocation failed
+ */
+#ifndef DGHGKS_H
+#define DGHGKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGHGKS_OK 0
+#define DGHGKS_EARG (-1)
+#define DGHGKS_EUNSUP (-2)
+#define DGHGKS_ECUDA (-3)
+#define DGHGKS_EPHYS (-4)
+#define DGHGKS_ENOMEM (-5)
+
+#define DGHGKS_FP64 0       /* flux and quadrature arithmetic in FP64 */
+#define DGHGKS_FP32_MIXED 1 /* flux/quadrature in FP32; stage arithmetic and reductions FP64 */
+
+typedef struct dghgks_ctx dghgks_ctx;
+
+/* Uniform Cartesian hexahedral mesh K_ijk = [x_{i-1/2}, x_{i+1/2}] x ... (Sec. 3).
+ * nx, ny, nz >= 1 cells on the box [lo, hi]; only periodic boundaries are
+ * supported (periodic[d] must be 1). */
+typedef struct {
+  int nx, ny, nz;
+  double lo[3], hi[3];
+  int periodic[3];
+} dghgks_mesh;
+
+/* n_q: Gauss points per direction (faces n_q^2, cells n_q^3); 0 = order+1.
+ * precision: DGHGKS_FP64 or DGHGKS_FP32_MIXED.
+ * tau_eps: tau = mu/p + tau_eps*dt (0 = the paper's tau = mu/p). */
+typedef struct {
+  int n_q;
+  int precision;
+  double tau_eps;
+} dghgks_opts;
+
+/* Create a solver for P_order elements (order 1, 2 or 3; n_q in {order, order+1},
+ * n_q >= 2) on `mesh`, for a gas with ratio of specific heats gamma, viscosity
+ * mu >= 0 and Prandtl number Pr > 0 (Pr = 1 is the BGK value used by the
+ * paper; Pr != 1 adds (1/Pr - 1) times the heat flux of the same distribution
+ * to the energy flux, which the paper does not define).  opts may be NULL
+ * (n_q = order+1, FP64, tau_eps = 0).  Uses the current CUDA device.
+ * Allocates the scratch: 2 stage buffers of the state size plus the face
+ * moments (3 * 10 * (k+1)(k+2)/2 values per cell in the flux precision). */
+int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, double Pr, const dghgks_opts* opts,
+                dghgks_ctx** out);
+
+/* Destroy a context and free its scratch.  NULL is ignored. */
+void dghgks_destroy(dghgks_ctx* ctx);
+
+/* Text of the last error of this context (or of a failed init if ctx is NULL). */
+const char* dghgks_last_error(const dghgks_ctx* ctx);
+
+/* Number of modal coefficients per cell and variable, N_m. */
+int dghgks_n_modes(const dghgks_ctx* ctx);
+
+/* Change the viscosity mu (>= 0) used by later calls. */
+int dghgks_set_mu(dghgks_ctx* ctx, double mu);
+
+/* One residual evaluation (Sec. 3, Eqs. operator/surface/volume with the
+ * fluxes of Eqs. flux and flux-2 fitted over [0, dt] and [0, dt/2]):
+ *   L = M^-1 R(Q), Lt = M^-1 R_t(Q).
+ * Q, L, Lt: device, state layout; L and Lt must not alias Q.  Asynchronous. */
+int dghgks_residual(dghgks_ctx* ctx, const double* Q, double dt, double* L, double* Lt, void* stream);
+
+/* One S2O4 step (Sec. 3, Eq. two-stage), in place on the device state Q:
+ *   Q* = Q + dt/2 L(Q) + dt^2/8 L_t(Q)
+ *   Q <- Q + dt L(Q) + dt^2/6 (L_t(Q) + 2 L_t(Q*)).
+ * Asynchronous; consecutive calls on one context must share a stream. */
+int dghgks_step(dghgks_ctx* ctx, double* Q, double dt, void* stream);
+
+/* nsteps S2O4 steps on a HOST state (pinned or pageable): copies Q_host to
+ * the device, steps, and copies the result back; if ek_host is not NULL it
+ * receives E_k (as dghgks_kinetic_energy with rho0) after every step.
+ * Synchronises.  Allocates one device state buffer on first use. */
+int dghgks_run_host(dghgks_ctx* ctx, double* Q_host, double dt, int nsteps, double rho0, double* ek_host,
+                    void* stream);
+
+/* Conserved totals sum_cells |K| Q_(var, mode 0), var = 0..4, in FP64.
+ * Synchronises; out is host memory (5 doubles). */
+int dghgks_totals(dghgks_ctx* ctx, const double* Q, double* out, void* stream);
+
+/* Volume-averaged kinetic energy E_k = 1/(rho0 |Omega|) int rho|U|^2/2
+ * (Sec. 5.3), by the n_q^3 cell Gauss rule, in FP64.  Synchronises; Ek is
+ * host memory. */
+int dghgks_kinetic_energy(dghgks_ctx* ctx, const double* Q, double rho0, double* Ek, void* stream);
+
+/* L2 norm over the domain of the difference of two modal states, variable
+ * var, in FP64 (orthogonal basis: sum_cells sum_n M_nn (A_n - B_n)^2).
+ * Synchronises; out is host memory. */
+int dghgks_l2_diff(dghgks_ctx* ctx, const double* A, const double* B, int var, double* out, void* stream);
+
+/* Synchronise `stream` and report the device error flag: DGHGKS_EPHYS if a
+ * non-physical state was met since the last check (the flag is then
+ * cleared), DGHGKS_ECUDA on a CUDA error, else 0. */
+int dghgks_status(dghgks_ctx* ctx, void* stream);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around
+ * every launch of this context.  enable = 1 starts (and clears) the record,
+ * 0 stops it.  Kernel kinds: 0..2 face flux for normals x, y, z; 3 cell
+ * kernel of a residual; 4 cell kernel of stage 1; 5 cell kernel of stage 2;
+ * 6 reductions.  dghgks_profile_read synchronises and returns, per kind,
+ * the summed milliseconds and the number of launches (arrays of length
+ * DGHGKS_NKINDS, host memory).  At most 65536 launches are recorded. */
+#define DGHGKS_NKINDS 7
+int dghgks_profile(dghgks_ctx* ctx, int enable);
+int dghgks_profile_read(dghgks_ctx* ctx, double* ms, int64_t* launches);
+
+/* Kernel launches made by this context since creation (all entry points). */
+int64_t dghgks_launch_count(const dghgks_ctx* ctx);
+
+/* Gauss-Legendre rule used on the device: nodes x[n] ascending on [-1,1],
+ * weights w[n] normalised to sum 1 (n = 1..5).  Host-only, no GPU needed. */
+int dghgks_gauss_rule(int n, double* x, double* w);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGHGKS_H */

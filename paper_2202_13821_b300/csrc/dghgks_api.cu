@@ -1,0 +1,497 @@
+// Host side of the C ABI declared in include/dghgks.h: context creation,
+// scratch allocation, kernel dispatch over (precision, order, n_q), the S2O4
+// driver and the FP64 reductions.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "dg_kernels.cuh"
+#include "dghgks.h"
+
+using namespace dghgks;
+
+namespace {
+
+constexpr int kRedBlocks = 148 * 8;  // reduction grid: 8 CTAs per SM
+constexpr int kProfMax = 65536;
+
+struct Ops;
+
+}  // namespace
+
+struct dghgks_ctx {
+  int device = 0;
+  int n[3] = {0, 0, 0};
+  long long ncell = 0;
+  double lo[3], hi[3], h[3], vol = 0;
+  int order = 0, nq = 0, nm = 0, nt = 0, precision = 0;
+  double gamma = 1.4, K = 2.0, mu = 0, Pr = 1, tau_eps = 0;
+  double* Qs = nullptr;   // Q* (stage-1 output)
+  double* Acc = nullptr;  // Q^n + dt L + dt^2/6 L_t
+  void* G = nullptr;      // face moments [3][10][NT][cells], flux precision
+  unsigned* flag = nullptr;
+  double* part = nullptr;  // reduction partials [kRedBlocks][5]
+  double* red = nullptr;   // reduction results (device)
+  double* red_host = nullptr;  // pinned
+  double* Qdev = nullptr;      // device state for dghgks_run_host
+  const Ops* ops = nullptr;
+  int64_t launches = 0;
+  // profiling: event pairs around launches
+  bool prof = false;
+  int prof_n = 0;
+  cudaEvent_t* prof_ev = nullptr;  // [2 * kProfMax]
+  int* prof_kind = nullptr;        // [kProfMax]
+  char err[512] = {0};
+};
+
+namespace {
+
+char g_init_err[512] = "";
+
+int fail(dghgks_ctx* c, int code, const char* fmt, ...) {
+  char* buf = c ? c->err : g_init_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_check(dghgks_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return DGHGKS_OK;
+  return fail(c, e == cudaErrorMemoryAllocation ? DGHGKS_ENOMEM : DGHGKS_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+template <class R>
+GasPar<R> gas_par(const dghgks_ctx* c, double dt) {
+  GasPar<R> g;
+  g.K = (R)c->K;
+  g.gm1 = (R)(c->gamma - 1.0);
+  g.mu = (R)c->mu;
+  g.tau_add = (R)(c->tau_eps * dt);
+  g.pr_fix = (R)(1.0 / c->Pr - 1.0);
+  g.dt = (R)dt;
+  g.inv_dt = (R)(1.0 / dt);
+  return g;
+}
+
+MeshDev mesh_dev(const dghgks_ctx* c) {
+  MeshDev m;
+  m.nx = c->n[0];
+  m.ny = c->n[1];
+  m.nz = c->n[2];
+  m.ncell = c->ncell;
+  for (int d = 0; d < 3; ++d) m.h[d] = c->h[d];
+  m.vol = c->vol;
+  return m;
+}
+
+// Bracket one launch with profiling events when profiling is on.
+struct ProfScope {
+  dghgks_ctx* c;
+  int slot = -1;
+  cudaStream_t s;
+  ProfScope(dghgks_ctx* c_, int kind, cudaStream_t s_) : c(c_), s(s_) {
+    if (c->prof && c->prof_n < kProfMax) {
+      slot = c->prof_n++;
+      c->prof_kind[slot] = kind;
+      cudaEventRecord(c->prof_ev[2 * slot], s);
+    }
+  }
+  ~ProfScope() {
+    if (slot >= 0) cudaEventRecord(c->prof_ev[2 * slot + 1], s);
+  }
+};
+
+struct Ops {
+  cudaError_t (*set_attrs)();
+  void (*faces)(dghgks_ctx*, const double*, double, cudaStream_t);
+  void (*cell)(dghgks_ctx*, int, const double*, double*, double*, const double*, double, cudaStream_t);
+  void (*ek)(dghgks_ctx*, const double*, cudaStream_t);
+  size_t r_size;
+};
+
+template <class R, int ORDER, int NQ>
+struct Impl {
+  using FS = FaceSmem<R, ORDER, NQ>;
+  using CS = CellSmem<R, ORDER, NQ>;
+
+  static cudaError_t set_attrs() {
+    cudaError_t e = cudaSuccess;
+#define DG_ATTR(fn, bytes)                                                                         \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes));
+    DG_ATTR((k_face<R, ORDER, NQ, 0>), FS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 1>), FS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 2>), FS::bytes)
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_RESIDUAL>), CS::bytes)
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1>), CS::bytes)
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE2>), CS::bytes)
+#undef DG_ATTR
+    return e;
+  }
+
+  static void faces(dghgks_ctx* c, const double* Q, double dt, cudaStream_t s) {
+    const GasPar<R> g = gas_par<R>(c, dt);
+    const MeshDev m = mesh_dev(c);
+    dim3 grid((c->n[0] + FB - 1) / FB, c->n[1], c->n[2]);
+    dim3 block(FB * NQ * NQ);
+    R* G = static_cast<R*>(c->G);
+    {
+      ProfScope ps(c, 0, s);
+      k_face<R, ORDER, NQ, 0><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
+    }
+    {
+      ProfScope ps(c, 1, s);
+      k_face<R, ORDER, NQ, 1><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
+    }
+    {
+      ProfScope ps(c, 2, s);
+      k_face<R, ORDER, NQ, 2><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
+    }
+    c->launches += 3;
+  }
+
+  static void cell(dghgks_ctx* c, int mode, const double* Qin, double* o0, double* o1, const double* acc, double dt,
+                   cudaStream_t s) {
+    const GasPar<R> g = gas_par<R>(c, dt);
+    const MeshDev m = mesh_dev(c);
+    constexpr int CB = CellTile<NQ>::CB;
+    dim3 grid((c->n[0] + CB - 1) / CB, c->n[1], c->n[2]);
+    dim3 block(CB * NQ * NQ * NQ);
+    const R* G = static_cast<const R*>(c->G);
+    ProfScope ps(c, 3 + mode, s);
+    if (mode == MODE_RESIDUAL)
+      k_cell<R, ORDER, NQ, MODE_RESIDUAL><<<grid, block, CS::bytes, s>>>(Qin, G, o0, o1, acc, g, m, dt, c->flag);
+    else if (mode == MODE_STAGE1)
+      k_cell<R, ORDER, NQ, MODE_STAGE1><<<grid, block, CS::bytes, s>>>(Qin, G, o0, o1, acc, g, m, dt, c->flag);
+    else
+      k_cell<R, ORDER, NQ, MODE_STAGE2><<<grid, block, CS::bytes, s>>>(Qin, G, o0, o1, acc, g, m, dt, c->flag);
+    c->launches += 1;
+  }
+
+  static void ek(dghgks_ctx* c, const double* Q, cudaStream_t s) {
+    ProfScope ps(c, 6, s);
+    k_ek_part<ORDER, NQ><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, c->ncell, c->part);
+    c->launches += 1;
+  }
+};
+
+#define DG_OPS(R, O, N) \
+  Ops { &Impl<R, O, N>::set_attrs, &Impl<R, O, N>::faces, &Impl<R, O, N>::cell, &Impl<R, O, N>::ek, sizeof(R) }
+
+const Ops kOps64_1_2 = DG_OPS(double, 1, 2);
+const Ops kOps64_2_2 = DG_OPS(double, 2, 2);
+const Ops kOps64_2_3 = DG_OPS(double, 2, 3);
+const Ops kOps32_1_2 = DG_OPS(float, 1, 2);
+const Ops kOps32_2_2 = DG_OPS(float, 2, 2);
+const Ops kOps32_2_3 = DG_OPS(float, 2, 3);
+
+const Ops* select_ops(int precision, int order, int nq) {
+  const bool f64 = precision == DGHGKS_FP64;
+  if (order == 1 && nq == 2) return f64 ? &kOps64_1_2 : &kOps32_1_2;
+  if (order == 2 && nq == 2) return f64 ? &kOps64_2_2 : &kOps32_2_2;
+  if (order == 2 && nq == 3) return f64 ? &kOps64_2_3 : &kOps32_2_3;
+  return nullptr;
+}
+
+template <int NM>
+__global__ void __launch_bounds__(RED_THREADS) k_l2diff_part(const double* __restrict__ A, const double* __restrict__ B,
+                                                             int var, long long nc, double* __restrict__ part) {
+  double acc[1] = {0};
+  for (long long c = (long long)blockIdx.x * RED_THREADS + threadIdx.x; c < nc; c += (long long)gridDim.x * RED_THREADS)
+#pragma unroll
+    for (int mm = 0; mm < NM; ++mm) {
+      const size_t idx = (size_t)(var * NM + mm) * nc + c;
+      const double d = A[idx] - B[idx];
+      acc[0] += d * d / (double)((2 * mode_exp(mm, 0) + 1) * (2 * mode_exp(mm, 1) + 1) * (2 * mode_exp(mm, 2) + 1));
+    }
+  block_reduce_store<1>(acc, part);
+}
+
+int after_launch(dghgks_ctx* c, const char* what) { return cuda_check(c, cudaGetLastError(), what); }
+
+int read_flag(dghgks_ctx* c, cudaStream_t s) {
+  unsigned f = 0;
+  int rc = cuda_check(c, cudaMemcpyAsync(&f, c->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "flag read");
+  if (rc) return rc;
+  rc = cuda_check(c, cudaStreamSynchronize(s), "stream sync");
+  if (rc) return rc;
+  if (f) {
+    cudaMemsetAsync(c->flag, 0, sizeof(unsigned), s);
+    cudaStreamSynchronize(s);
+    return fail(c, DGHGKS_EPHYS, "non-physical state (rho <= 0 or p <= 0) met at a quadrature point");
+  }
+  return DGHGKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dghgks_gauss_rule(int n, double* x, double* w) {
+  if (n < 1 || n > 5 || !x || !w) return DGHGKS_EARG;
+  for (int a = 0; a < n; ++a) {
+    x[a] = gauss_x(n, a);
+    w[a] = gauss_w(n, a);
+  }
+  return DGHGKS_OK;
+}
+
+int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, double Pr, const dghgks_opts* opts,
+                dghgks_ctx** out) {
+  if (!out) return fail(nullptr, DGHGKS_EARG, "out is NULL");
+  *out = nullptr;
+  if (!mesh) return fail(nullptr, DGHGKS_EARG, "mesh is NULL");
+  if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || mesh->ny > 65535 || mesh->nz > 65535)
+    return fail(nullptr, DGHGKS_EARG, "bad mesh size %d x %d x %d", mesh->nx, mesh->ny, mesh->nz);
+  for (int d = 0; d < 3; ++d) {
+    if (!(mesh->hi[d] > mesh->lo[d])) return fail(nullptr, DGHGKS_EARG, "mesh hi <= lo along axis %d", d);
+    if (mesh->periodic[d] != 1) return fail(nullptr, DGHGKS_EUNSUP, "only periodic boundaries are supported");
+  }
+  if (!(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0)) return fail(nullptr, DGHGKS_EARG, "bad gas parameters");
+  const int nq = (opts && opts->n_q) ? opts->n_q : order + 1;
+  const int precision = opts ? opts->precision : DGHGKS_FP64;
+  const double tau_eps = opts ? opts->tau_eps : 0.0;
+  if (precision != DGHGKS_FP64 && precision != DGHGKS_FP32_MIXED)
+    return fail(nullptr, DGHGKS_EARG, "precision must be DGHGKS_FP64 or DGHGKS_FP32_MIXED");
+  if (!(tau_eps >= 0.0)) return fail(nullptr, DGHGKS_EARG, "tau_eps must be >= 0");
+  const Ops* ops = select_ops(precision, order, nq);
+  if (!ops) return fail(nullptr, DGHGKS_EUNSUP, "unsupported order %d with n_q %d", order, nq);
+
+  dghgks_ctx* c = new (std::nothrow) dghgks_ctx();
+  if (!c) return fail(nullptr, DGHGKS_ENOMEM, "host allocation failed");
+  cudaGetDevice(&c->device);
+  c->n[0] = mesh->nx;
+  c->n[1] = mesh->ny;
+  c->n[2] = mesh->nz;
+  c->ncell = (long long)mesh->nx * mesh->ny * mesh->nz;
+  c->vol = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    c->lo[d] = mesh->lo[d];
+    c->hi[d] = mesh->hi[d];
+    c->h[d] = (mesh->hi[d] - mesh->lo[d]) / c->n[d];
+    c->vol *= c->h[d];
+  }
+  c->order = order;
+  c->nq = nq;
+  c->nm = n_modes(order);
+  c->nt = n_tmodes(order);
+  c->precision = precision;
+  c->gamma = gamma;
+  c->K = (5.0 - 3.0 * gamma) / (gamma - 1.0);
+  c->mu = mu;
+  c->Pr = Pr;
+  c->tau_eps = tau_eps;
+  c->ops = ops;
+
+  const size_t state = sizeof(double) * 5 * (size_t)c->nm * c->ncell;
+  const size_t gbytes = ops->r_size * 30 * (size_t)c->nt * c->ncell;
+  int rc = DGHGKS_OK;
+  if (!rc) rc = cuda_check(c, ops->set_attrs(), "cudaFuncSetAttribute");
+  if (!rc) rc = cuda_check(c, cudaMalloc(&c->Qs, state), "cudaMalloc(Q*)");
+  if (!rc) rc = cuda_check(c, cudaMalloc(&c->Acc, state), "cudaMalloc(Acc)");
+  if (!rc) rc = cuda_check(c, cudaMalloc(&c->G, gbytes), "cudaMalloc(face moments)");
+  if (!rc) rc = cuda_check(c, cudaMalloc(&c->flag, sizeof(unsigned)), "cudaMalloc(flag)");
+  if (!rc) rc = cuda_check(c, cudaMalloc(&c->part, sizeof(double) * 5 * kRedBlocks), "cudaMalloc(partials)");
+  if (!rc) rc = cuda_check(c, cudaMalloc(&c->red, sizeof(double) * 8), "cudaMalloc(red)");
+  if (!rc) rc = cuda_check(c, cudaMallocHost(&c->red_host, sizeof(double) * 8), "cudaMallocHost");
+  if (!rc) rc = cuda_check(c, cudaMemset(c->flag, 0, sizeof(unsigned)), "cudaMemset(flag)");
+  if (rc) {
+    snprintf(g_init_err, sizeof(g_init_err), "%s", c->err);
+    dghgks_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return DGHGKS_OK;
+}
+
+void dghgks_destroy(dghgks_ctx* c) {
+  if (!c) return;
+  if (c->prof_ev) {
+    for (int e = 0; e < 2 * kProfMax; ++e) cudaEventDestroy(c->prof_ev[e]);
+    delete[] c->prof_ev;
+    delete[] c->prof_kind;
+  }
+  cudaFree(c->Qs);
+  cudaFree(c->Acc);
+  cudaFree(c->G);
+  cudaFree(c->flag);
+  cudaFree(c->part);
+  cudaFree(c->red);
+  cudaFree(c->Qdev);
+  if (c->red_host) cudaFreeHost(c->red_host);
+  delete c;
+}
+
+const char* dghgks_last_error(const dghgks_ctx* c) { return c ? c->err : g_init_err; }
+
+int dghgks_n_modes(const dghgks_ctx* c) { return c ? c->nm : DGHGKS_EARG; }
+
+int64_t dghgks_launch_count(const dghgks_ctx* c) { return c ? c->launches : 0; }
+
+int dghgks_set_mu(dghgks_ctx* c, double mu) {
+  if (!c) return DGHGKS_EARG;
+  if (!(mu >= 0.0)) return fail(c, DGHGKS_EARG, "mu must be >= 0");
+  c->mu = mu;
+  return DGHGKS_OK;
+}
+
+int dghgks_residual(dghgks_ctx* c, const double* Q, double dt, double* L, double* Lt, void* stream) {
+  if (!c) return DGHGKS_EARG;
+  if (!Q || !L || !Lt) return fail(c, DGHGKS_EARG, "NULL state or output pointer");
+  if (!(dt > 0)) return fail(c, DGHGKS_EARG, "dt must be > 0");
+  if (L == Q || Lt == Q || L == Lt) return fail(c, DGHGKS_EARG, "L, Lt and Q must be distinct buffers");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->ops->faces(c, Q, dt, s);
+  c->ops->cell(c, MODE_RESIDUAL, Q, L, Lt, nullptr, dt, s);
+  return after_launch(c, "residual launch");
+}
+
+int dghgks_step(dghgks_ctx* c, double* Q, double dt, void* stream) {
+  if (!c) return DGHGKS_EARG;
+  if (!Q) return fail(c, DGHGKS_EARG, "Q is NULL");
+  if (!(dt > 0)) return fail(c, DGHGKS_EARG, "dt must be > 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // stage 1 at Q^n
+  c->ops->faces(c, Q, dt, s);
+  c->ops->cell(c, MODE_STAGE1, Q, c->Qs, c->Acc, nullptr, dt, s);
+  // stage 2 at Q* (same dt for the flux fit); only L_t(Q*) enters
+  c->ops->faces(c, c->Qs, dt, s);
+  c->ops->cell(c, MODE_STAGE2, c->Qs, Q, nullptr, c->Acc, dt, s);
+  return after_launch(c, "step launch");
+}
+
+int dghgks_totals(dghgks_ctx* c, const double* Q, double* out, void* stream) {
+  if (!c) return DGHGKS_EARG;
+  if (!Q || !out) return fail(c, DGHGKS_EARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (c->nm) {
+    case 4: k_totals_part<4><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, c->ncell, c->part); break;
+    case 10: k_totals_part<10><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, c->ncell, c->part); break;
+    default: k_totals_part<20><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, c->ncell, c->part); break;
+  }
+  k_reduce_final<5><<<1, RED_THREADS, 0, s>>>(c->part, kRedBlocks, c->vol, c->red);
+  c->launches += 2;
+  if (int rc = after_launch(c, "totals launch")) return rc;
+  if (int rc = cuda_check(c, cudaMemcpyAsync(c->red_host, c->red, 5 * sizeof(double), cudaMemcpyDeviceToHost, s),
+                          "totals copy"))
+    return rc;
+  if (int rc = cuda_check(c, cudaStreamSynchronize(s), "totals sync")) return rc;
+  memcpy(out, c->red_host, 5 * sizeof(double));
+  return DGHGKS_OK;
+}
+
+static int enqueue_ek(dghgks_ctx* c, const double* Q, double rho0, double* dst_dev, cudaStream_t s) {
+  c->ops->ek(c, Q, s);
+  const double omega = c->vol * (double)c->ncell;
+  k_reduce_final<1><<<1, RED_THREADS, 0, s>>>(c->part, kRedBlocks, c->vol / (rho0 * omega), dst_dev);
+  c->launches += 1;
+  return after_launch(c, "kinetic energy launch");
+}
+
+int dghgks_kinetic_energy(dghgks_ctx* c, const double* Q, double rho0, double* Ek, void* stream) {
+  if (!c) return DGHGKS_EARG;
+  if (!Q || !Ek) return fail(c, DGHGKS_EARG, "NULL argument");
+  if (!(rho0 > 0)) return fail(c, DGHGKS_EARG, "rho0 must be > 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (int rc = enqueue_ek(c, Q, rho0, c->red, s)) return rc;
+  if (int rc = cuda_check(c, cudaMemcpyAsync(c->red_host, c->red, sizeof(double), cudaMemcpyDeviceToHost, s),
+                          "E_k copy"))
+    return rc;
+  if (int rc = cuda_check(c, cudaStreamSynchronize(s), "E_k sync")) return rc;
+  *Ek = c->red_host[0];
+  return DGHGKS_OK;
+}
+
+int dghgks_l2_diff(dghgks_ctx* c, const double* A, const double* B, int var, double* out, void* stream) {
+  if (!c) return DGHGKS_EARG;
+  if (!A || !B || !out || var < 0 || var > 4) return fail(c, DGHGKS_EARG, "bad argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (c->nm) {
+    case 4: k_l2diff_part<4><<<kRedBlocks, RED_THREADS, 0, s>>>(A, B, var, c->ncell, c->part); break;
+    case 10: k_l2diff_part<10><<<kRedBlocks, RED_THREADS, 0, s>>>(A, B, var, c->ncell, c->part); break;
+    default: k_l2diff_part<20><<<kRedBlocks, RED_THREADS, 0, s>>>(A, B, var, c->ncell, c->part); break;
+  }
+  k_reduce_final<1><<<1, RED_THREADS, 0, s>>>(c->part, kRedBlocks, c->vol, c->red);
+  c->launches += 2;
+  if (int rc = after_launch(c, "l2 diff launch")) return rc;
+  if (int rc = cuda_check(c, cudaMemcpyAsync(c->red_host, c->red, sizeof(double), cudaMemcpyDeviceToHost, s),
+                          "l2 copy"))
+    return rc;
+  if (int rc = cuda_check(c, cudaStreamSynchronize(s), "l2 sync")) return rc;
+  *out = sqrt(c->red_host[0]);
+  return DGHGKS_OK;
+}
+
+int dghgks_run_host(dghgks_ctx* c, double* Q_host, double dt, int nsteps, double rho0, double* ek_host,
+                    void* stream) {
+  if (!c) return DGHGKS_EARG;
+  if (!Q_host || nsteps < 0 || !(dt > 0) || !(rho0 > 0)) return fail(c, DGHGKS_EARG, "bad argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t state = sizeof(double) * 5 * (size_t)c->nm * c->ncell;
+  if (!c->Qdev)
+    if (int rc = cuda_check(c, cudaMalloc(&c->Qdev, state), "cudaMalloc(run state)")) return rc;
+  if (int rc = cuda_check(c, cudaMemcpyAsync(c->Qdev, Q_host, state, cudaMemcpyHostToDevice, s), "H2D state"))
+    return rc;
+  for (int n = 0; n < nsteps; ++n) {
+    if (int rc = dghgks_step(c, c->Qdev, dt, stream)) return rc;
+    if (ek_host) {
+      if (int rc = enqueue_ek(c, c->Qdev, rho0, c->red + (n % 8), s)) return rc;
+      if (int rc = cuda_check(c, cudaMemcpyAsync(c->red_host + (n % 8), c->red + (n % 8), sizeof(double),
+                                                 cudaMemcpyDeviceToHost, s),
+                              "D2H E_k"))
+        return rc;
+      if (n % 8 == 7 || n == nsteps - 1) {
+        if (int rc = cuda_check(c, cudaStreamSynchronize(s), "E_k sync")) return rc;
+        for (int m = n - (n % 8); m <= n; ++m) ek_host[m] = c->red_host[m % 8];
+      }
+    }
+  }
+  if (int rc = cuda_check(c, cudaMemcpyAsync(Q_host, c->Qdev, state, cudaMemcpyDeviceToHost, s), "D2H state"))
+    return rc;
+  return read_flag(c, s);
+}
+
+int dghgks_profile(dghgks_ctx* c, int enable) {
+  if (!c) return DGHGKS_EARG;
+  if (enable && !c->prof_ev) {
+    c->prof_ev = new (std::nothrow) cudaEvent_t[2 * kProfMax];
+    c->prof_kind = new (std::nothrow) int[kProfMax];
+    if (!c->prof_ev || !c->prof_kind) return fail(c, DGHGKS_ENOMEM, "profile buffers");
+    for (int e = 0; e < 2 * kProfMax; ++e)
+      if (int rc = cuda_check(c, cudaEventCreate(&c->prof_ev[e]), "cudaEventCreate")) return rc;
+  }
+  c->prof = enable != 0;
+  if (enable) c->prof_n = 0;
+  return DGHGKS_OK;
+}
+
+int dghgks_profile_read(dghgks_ctx* c, double* ms, int64_t* launches) {
+  if (!c || !ms || !launches) return DGHGKS_EARG;
+  for (int k = 0; k < DGHGKS_NKINDS; ++k) {
+    ms[k] = 0;
+    launches[k] = 0;
+  }
+  for (int i = 0; i < c->prof_n; ++i) {
+    if (int rc = cuda_check(c, cudaEventSynchronize(c->prof_ev[2 * i + 1]), "event sync")) return rc;
+    float t = 0;
+    if (int rc = cuda_check(c, cudaEventElapsedTime(&t, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]), "elapsed"))
+      return rc;
+    ms[c->prof_kind[i]] += t;
+    launches[c->prof_kind[i]] += 1;
+  }
+  return DGHGKS_OK;
+}
+
+int dghgks_status(dghgks_ctx* c, void* stream) {
+  if (!c) return DGHGKS_EARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (int rc = cuda_check(c, cudaGetLastError(), "pending error")) return rc;
+  return read_flag(c, s);
+}
+
+}  // extern "C"

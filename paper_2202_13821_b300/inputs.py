@@ -64,7 +64,7 @@ def modal_state(prim_fn, n, order, lo, hi, gamma=1.4, perturb=0.0, seed=SEED, **
     normal perturbation added to every coefficient, relative to the largest
     |cell mean| of each variable.
     """
-    n = tuple(int(v) for v in n)
+    n = (int(n),) * 3 if np.isscalar(n) else tuple(int(v) for v in n)
     (X, Y, Z), h = _centres(n, lo, hi)
     nm = n_modes(order)
     Q = np.zeros((5, nm, n[2], n[1], n[0]))
@@ -88,7 +88,11 @@ def advection_state(n, order, perturb=0.0, seed=SEED, gamma=1.4, amp=0.2):
 
 def tgv_state(n, order, perturb=0.0, seed=SEED, gamma=1.4, Ma=0.1, isothermal=False):
     lo, hi = (-np.pi,) * 3, (np.pi,) * 3
-    return modal_state(tgv_prim, n, order, lo, hi, gamma, perturb, seed, Ma=Ma, gamma=gamma, isothermal=isothermal)
+
+    def prim(x, y, z):
+        return tgv_prim(x, y, z, Ma=Ma, gamma=gamma, isothermal=isothermal)
+
+    return modal_state(prim, n, order, lo, hi, gamma, perturb, seed)
 
 
 def random_state(n, order, seed=SEED, rho=(0.5, 2.0), vel=1.0, p=(0.5, 3.0), modes_rel=0.02, gamma=1.4):

@@ -1,0 +1,168 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance (FP64 path): for each output array (L, L_t, or a state increment)
+and each variable v, max |gpu - oracle| <= 1e-11 * max |oracle| over all cells
+and modes of that variable.  The two sides evaluate the same formulas in a
+different order (closed-form vs LU slope solves, compile-time moment
+products vs expanded monomials, CUDA vs glibc exp/erfc), so they agree to
+rounding amplified by the cancellations of the method (pressure fluxes that
+cancel across a cell, equilibrium minus free-transport terms of d_t F).
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def api(torch):
+    from paper_2202_13821_b300 import api, build
+
+    build.build()
+    api.load()
+    return api
+
+
+def per_var_err(a, b):
+    a = np.asarray(a).reshape(5, -1)
+    b = np.asarray(b).reshape(5, -1)
+    scale = np.abs(b).max(axis=1)
+    scale = np.where(scale > 0, scale, 1.0)
+    return np.abs(a - b).max(axis=1) / scale
+
+
+def make(api, orc, n, lo, hi, order, nq, mu=0.0, Pr=1.0, tau_eps=0.0, precision=0):
+    s = api.Solver(n, lo, hi, order=order, mu=mu, Pr=Pr, n_q=nq, precision=precision, tau_eps=tau_eps)
+    pb = orc.Problem(order=order, nq=nq, n=tuple(n), lo=tuple(lo), hi=tuple(hi), mu=mu, Pr=Pr, tau_eps=tau_eps)
+    return s, pb
+
+
+def residual_pair(torch, s, pb, orc, Q, dt):
+    Qd = torch.from_numpy(Q).cuda()
+    L, Lt = s.residual(Qd, dt)
+    torch.cuda.synchronize()
+    s.status()
+    Lo, Lto = orc.residual(pb, Q, dt)
+    return L.cpu().numpy(), Lt.cpu().numpy(), Lo, Lto
+
+
+ADV = dict(lo=(0.0,) * 3, hi=(2.0,) * 3)
+TGV = dict(lo=(-math.pi,) * 3, hi=(math.pi,) * 3)
+
+
+@pytest.mark.parametrize("n", [(8, 8, 8), (37, 5, 6), (1, 3, 2)])
+def test_advection_p1_residual(torch, api, orc, n):
+    from paper_2202_13821_b300 import inputs
+
+    s, pb = make(api, orc, n, order=1, nq=2, tau_eps=0.01, **ADV)
+    Q = inputs.modal_state(inputs.advection_prim, n, 1, ADV["lo"], ADV["hi"], perturb=1e-3)
+    L, Lt, Lo, Lto = residual_pair(torch, s, pb, orc, Q, 8.2e-3)
+    assert per_var_err(L, Lo).max() < RTOL
+    assert per_var_err(Lt, Lto).max() < RTOL
+
+
+@pytest.mark.parametrize("nq", [3, 2])
+@pytest.mark.parametrize("Pr", [1.0, 0.72])
+@pytest.mark.parametrize("n", [(8, 8, 8), (35, 9, 4)])
+def test_tgv_p2_residual(torch, api, orc, n, Pr, nq):
+    from paper_2202_13821_b300 import inputs
+
+    s, pb = make(api, orc, n, order=2, nq=nq, mu=1 / 1600, Pr=Pr, **TGV)
+    Q = inputs.modal_state(inputs.tgv_prim, n, 2, TGV["lo"], TGV["hi"], perturb=1e-3)
+    dt = 1.3e-3
+    L, Lt, Lo, Lto = residual_pair(torch, s, pb, orc, Q, dt)
+    assert per_var_err(L, Lo).max() < RTOL
+    assert per_var_err(Lt, Lto).max() < RTOL
+
+
+@pytest.mark.parametrize("order,nq", [(1, 2), (2, 3), (2, 2)])
+@pytest.mark.parametrize("mu,tau_eps,Pr", [(0.0, 0.0, 1.0), (5e-3, 0.05, 1.0), (2e-3, 0.0, 0.72)])
+def test_random_discontinuous_states(torch, api, orc, order, nq, mu, tau_eps, Pr):
+    from paper_2202_13821_b300 import inputs
+
+    n = (5, 4, 3)
+    s, pb = make(api, orc, n, lo=(0, 0, 0), hi=(1.0, 0.8, 0.6), order=order, nq=nq, mu=mu, Pr=Pr, tau_eps=tau_eps)
+    Q = inputs.random_state(n, order, seed=7 + order)
+    L, Lt, Lo, Lto = residual_pair(torch, s, pb, orc, Q, 2e-3)
+    assert per_var_err(L, Lo).max() < RTOL
+    assert per_var_err(Lt, Lto).max() < RTOL
+
+
+@pytest.mark.parametrize("order,nq,case", [(1, 2, "adv"), (2, 3, "tgv")])
+def test_s2o4_step_parity(torch, api, orc, order, nq, case):
+    from paper_2202_13821_b300 import inputs
+
+    n = (6, 7, 5)
+    if case == "adv":
+        s, pb = make(api, orc, n, order=order, nq=nq, tau_eps=0.01, **ADV)
+        Q = inputs.modal_state(inputs.advection_prim, n, order, ADV["lo"], ADV["hi"], perturb=1e-3)
+        dt = 8e-3
+    else:
+        s, pb = make(api, orc, n, order=order, nq=nq, mu=1 / 1600, Pr=0.72, **TGV)
+        Q = inputs.modal_state(inputs.tgv_prim, n, order, TGV["lo"], TGV["hi"], perturb=1e-3)
+        dt = 5e-3
+    Qd = torch.from_numpy(Q).cuda()
+    s.step(Qd, dt, 2)
+    s.status()
+    Qo = orc.step(pb, Q, dt, 2)
+    dg = Qd.cpu().numpy() - Q
+    do = Qo - Q
+    assert per_var_err(dg, do).max() < RTOL
+
+
+def test_sampled_cells_full_size_tgv_256(torch, api, orc):
+    """Bench launch configuration (TGV 256^3, P2, n_q = 3, FP64) on sampled cells."""
+    from paper_2202_13821_b300 import inputs
+
+    n = (256, 256, 256)
+    s, pb = make(api, orc, n, order=2, nq=3, mu=1 / 1600, Pr=0.72, **TGV)
+    Q = inputs.tgv_state(256, 2)
+    dt = inputs.tgv_dt(256, 2)
+    Qd = torch.from_numpy(Q).cuda()
+    L, Lt = s.residual(Qd, dt)
+    torch.cuda.synchronize()
+    s.status()
+    rng = np.random.default_rng(0)
+    cells = np.concatenate([[0, 255, 256 * 256 - 1, 256 ** 3 - 1, 256 * 255 + 31, 256 * 256 * 128 + 33],
+                            rng.integers(0, 256 ** 3, 40)])
+    Lo, Lto = orc.residual_cells(pb, Q, dt, cells)
+    Lc = L.reshape(5, 10, -1)[:, :, cells].permute(2, 0, 1).cpu().numpy()
+    Ltc = Lt.reshape(5, 10, -1)[:, :, cells].permute(2, 0, 1).cpu().numpy()
+    # scale per variable over the sampled cells
+    for A, B in ((Lc, Lo), (Ltc, Lto)):
+        scale = np.abs(B).max(axis=(0, 2))
+        err = np.abs(A - B).max(axis=(0, 2)) / scale
+        assert err.max() < RTOL, err
+
+
+def test_totals_and_kinetic_energy(torch, api, orc):
+    from paper_2202_13821_b300 import inputs
+
+    n = (12, 10, 9)
+    s, pb = make(api, orc, n, order=2, nq=3, mu=1 / 1600, **TGV)
+    Q = inputs.modal_state(inputs.tgv_prim, n, 2, TGV["lo"], TGV["hi"], perturb=1e-3)
+    Qd = torch.from_numpy(Q).cuda()
+    np.testing.assert_allclose(s.totals(Qd), orc.totals(pb, Q), rtol=1e-13, atol=1e-13)
+    assert abs(s.kinetic_energy(Qd) - orc.kinetic_energy(pb, Q)) < 1e-14
+    # L2 difference through the mass matrix against a direct numpy evaluation
+    Q2 = Q.copy()
+    Q2[0] += 1e-3 * np.random.default_rng(1).standard_normal(Q2[0].shape)
+    h = [(TGV["hi"][d] - TGV["lo"][d]) / n[d] for d in range(3)]
+    md = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2), (1, 1, 0), (1, 0, 1), (0, 1, 1)]
+    M = np.array([np.prod(h) / np.prod([2 * e + 1 for e in m]) for m in md])
+    want = math.sqrt(np.sum(M[:, None, None, None] * (Q2[0] - Q[0]) ** 2))
+    got = s.l2_diff(torch.from_numpy(Q2).cuda(), Qd, 0)
+    assert abs(got - want) <= 1e-12 * want
