@@ -116,17 +116,21 @@ def residual(pb: Problem, Q: np.ndarray, dt: float):
     return L, Lt
 
 
-def residual_cells(pb: Problem, Q: np.ndarray, dt: float, cells: np.ndarray):
-    """(L, L_t) of selected cells (flat index i + nx (j + ny k)), shape [n][5][modes]."""
+def residual_cells(pb: Problem, Q: np.ndarray, dt: float, cells: np.ndarray, scales: bool = False):
+    """(L, L_t) of selected cells (flat index i + nx (j + ny k)), shape [n][5][modes].
+
+    With ``scales=True`` also returns (A, A_t): M^-1 times the sums of the
+    absolute values of the contributions to R and R_t (the rounding scale).
+    """
     Q = np.ascontiguousarray(Q, dtype=np.float64)
     cells = np.ascontiguousarray(cells, dtype=np.int64)
     out = np.zeros((len(cells), 5, pb.n_modes))
-    outt = np.zeros_like(out)
+    outt, A, At = np.zeros_like(out), np.zeros_like(out), np.zeros_like(out)
     c = pb.cfg()
     _check(lib().orc_residual_cells(ctypes.byref(c), _p(Q), ctypes.c_double(dt),
                                     cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                                    ctypes.c_int64(len(cells)), _p(out), _p(outt)), "residual_cells")
-    return out, outt
+                                    ctypes.c_int64(len(cells)), _p(out), _p(outt), _p(A), _p(At)), "residual_cells")
+    return (out, outt, A, At) if scales else (out, outt)
 
 
 def step(pb: Problem, Q: np.ndarray, dt: float, nsteps: int = 1) -> np.ndarray:

@@ -688,14 +688,19 @@ inline int wrap(int i, int n) { return ((i % n) + n) % n; }
 // R and R_t of one cell, divided by the mass matrix (-> L, L_t), written as
 // [var][mode].  Each cell evaluates its six faces itself; a face evaluated
 // from both of its cells gets identical arguments (left = lower index).
+// If A, At are given they receive M^-1 times the sums of the absolute values
+// of the same contributions: the scale against which rounding in L, L_t is
+// measured (the residual is a sum with heavy cancellation).
 template <class T>
-inline bool residual_cell(const Grid& G, const Phys<T>& ph, const T* Q, double dt, int i, int j, int k, T* L, T* Lt) {
+inline bool residual_cell(const Grid& G, const Phys<T>& ph, const T* Q, double dt, int i, int j, int k, T* L, T* Lt,
+                          double* A = nullptr, double* At = nullptr) {
   const std::vector<Mode> md = mode_list(G.order);
   const int nm = (int)md.size(), nq = G.nq;
   double gx[8], gw[8];
   gauss_rule(nq, gx, gw);
   const double vol = G.h(0) * G.h(1) * G.h(2);
   std::vector<T> R(5 * nm, T(0.0)), Rt(5 * nm, T(0.0));
+  std::vector<double> Ra(5 * nm, 0.0), Rta(5 * nm, 0.0);
 
   // volume integral: sum_m w_m |K| F_v(x_m) . grad B_n(x_m)
   for (int a = 0; a < nq; ++a)
@@ -713,6 +718,8 @@ inline bool residual_cell(const Grid& G, const Phys<T>& ph, const T* Q, double d
             for (int d = 0; d < 3; ++d) {
               R[v * nm + m] += w * F[d][v] * gb[d];
               Rt[v * nm + m] += w * Ft[d][v] * gb[d];
+              Ra[v * nm + m] += std::fabs(w * value_of(F[d][v]) * gb[d]);
+              Rta[v * nm + m] += std::fabs(w * value_of(Ft[d][v]) * gb[d]);
             }
         }
       }
@@ -745,6 +752,8 @@ inline bool residual_cell(const Grid& G, const Phys<T>& ph, const T* Q, double d
             for (int v = 0; v < 5; ++v) {
               R[v * nm + m] -= w * (double)s * F[v] * bn;
               Rt[v * nm + m] -= w * (double)s * Ft[v] * bn;
+              Ra[v * nm + m] += std::fabs(w * value_of(F[v]) * bn);
+              Rta[v * nm + m] += std::fabs(w * value_of(Ft[v]) * bn);
             }
           }
         }
@@ -756,6 +765,8 @@ inline bool residual_cell(const Grid& G, const Phys<T>& ph, const T* Q, double d
     for (int v = 0; v < 5; ++v) {
       L[v * nm + m] = R[v * nm + m] / M;
       Lt[v * nm + m] = Rt[v * nm + m] / M;
+      if (A) A[v * nm + m] = Ra[v * nm + m] / M;
+      if (At) At[v * nm + m] = Rta[v * nm + m] / M;
     }
   }
   return true;

@@ -143,9 +143,9 @@ int orc_residual(const orc_cfg* c, const double* Q, double dt, double* L, double
 }
 
 // Residual of selected cells (flat cell index i + nx (j + ny k)); L, Lt are
-// [ncells][5][n_modes].
+// [ncells][5][n_modes].  A, At (may be NULL) receive the absolute-value scales.
 int orc_residual_cells(const orc_cfg* c, const double* Q, double dt, const int64_t* cells, int64_t ncells, double* L,
-                       double* Lt) {
+                       double* Lt, double* A, double* At) {
   orc::Grid G;
   if (!make_grid(c, G) || !(dt > 0)) return -1;
   auto ph = make_phys<double>(c, c->mu);
@@ -155,7 +155,8 @@ int orc_residual_cells(const orc_cfg* c, const double* Q, double dt, const int64
   for (int64_t s = 0; s < ncells; ++s) {
     int64_t id = cells[s];
     int i = (int)(id % G.n[0]), j = (int)((id / G.n[0]) % G.n[1]), k = (int)(id / ((int64_t)G.n[0] * G.n[1]));
-    if (!orc::residual_cell(G, ph, Q, dt, i, j, k, L + s * 5 * nm, Lt + s * 5 * nm)) {
+    if (!orc::residual_cell(G, ph, Q, dt, i, j, k, L + s * 5 * nm, Lt + s * 5 * nm, A ? A + s * 5 * nm : nullptr,
+                            At ? At + s * 5 * nm : nullptr)) {
 #pragma omp atomic write
       rc = -4;
     }

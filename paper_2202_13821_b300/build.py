@@ -1,6 +1,7 @@
 """Build libdghgks.so (CUDA, sm_103a) in-tree with nvcc."""
 from __future__ import annotations
 
+import json
 import os
 import subprocess
 import sys
@@ -9,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SO = os.path.join(HERE, "libdghgks.so")
 SOURCES = [os.path.join(HERE, "csrc", "dghgks_api.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))] + [
+DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc")) if f.endswith((".cu", ".cuh"))] + [
     os.path.join(ROOT, "include", "dghgks.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
@@ -23,7 +24,38 @@ def nvcc() -> str:
     return "nvcc"
 
 
+OPCOUNT_JSON = os.path.join(HERE, "opcount.json")
+
+
+def build_opcount(force: bool = False) -> str:
+    """Compile and run the host operation counter; writes opcount.json."""
+    src = os.path.join(HERE, "csrc", "opcount.cpp")
+    deps = [src, os.path.join(HERE, "csrc", "gks_point.cuh")]
+    if not force and os.path.exists(OPCOUNT_JSON) and os.path.getmtime(OPCOUNT_JSON) >= max(map(os.path.getmtime, deps)):
+        return OPCOUNT_JSON
+    exe = os.path.join(HERE, "opcount.bin")
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), "include")
+    subprocess.run(["g++", "-std=c++17", "-O1", "-Wno-unknown-pragmas", "-I", cuda_inc, "-I", "/usr/local/cuda/include",
+                    "-o", exe, src], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    rows = [json.loads(l) for l in out.splitlines() if l.strip()]
+    with open(OPCOUNT_JSON + ".tmp", "w") as f:
+        json.dump(rows, f, indent=1)
+    os.replace(OPCOUNT_JSON + ".tmp", OPCOUNT_JSON)
+    os.remove(exe)
+    return OPCOUNT_JSON
+
+
+def opcounts(order: int, n_q: int, pr_fix: bool) -> dict:
+    build_opcount()
+    for r in json.load(open(OPCOUNT_JSON)):
+        if r["order"] == order and r["n_q"] == n_q and r["pr_fix"] == pr_fix:
+            return r
+    raise KeyError((order, n_q, pr_fix))
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    build_opcount(force)
     newest = max(os.path.getmtime(f) for f in DEPS if os.path.exists(f))
     if not force and os.path.exists(SO) and os.path.getmtime(SO) >= newest:
         return SO

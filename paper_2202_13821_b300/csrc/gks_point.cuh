@@ -23,7 +23,19 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cmath>
+
+// Point functions compile for the device and, for the operation counter, for
+// the host with a counting scalar type.
+#ifndef DG_HD
+#define DG_HD __host__ __device__ __forceinline__
+#endif
+
 namespace dghgks {
+
+using std::erfc;
+using std::exp;
+using std::sqrt;
 
 template <class R>
 struct GasPar {
@@ -45,14 +57,14 @@ struct MomTab {
 };
 
 template <class R>
-__device__ __forceinline__ void raw_moments_tail(R* m, R U, R h) {
+DG_HD void raw_moments_tail(R* m, R U, R h) {
   // <c^(n+2)> = U <c^(n+1)> + (n+1) h <c^n> with h = 1/(2 lambda)
 #pragma unroll
   for (int n = 0; n < 5; ++n) m[n + 2] = U * m[n + 1] + R(n + 1) * h * m[n];
 }
 
 template <class R>
-__device__ __forceinline__ void full_line(R* m, R U, R h) {
+DG_HD void full_line(R* m, R U, R h) {
   m[0] = R(1);
   m[1] = U;
   raw_moments_tail(m, U, h);
@@ -60,7 +72,7 @@ __device__ __forceinline__ void full_line(R* m, R U, R h) {
 
 // u > 0 (sgn = +1) or u < 0 (sgn = -1) half line
 template <class R>
-__device__ __forceinline__ void half_line(R* m, R U, R lam, R h, int sgn) {
+DG_HD void half_line(R* m, R U, R lam, R h, int sgn) {
   const R sl = sqrt(lam);
   const R e = exp(-lam * U * U) * R(0.28209479177387814347) / sl;  // exp(-lam U^2) / (2 sqrt(pi lam))
   if (sgn > 0) {
@@ -80,7 +92,7 @@ struct Prim {
 
 // conservative -> (rho, U, V, W, lambda = rho / 2p); false if rho or p is not positive
 template <class R>
-__device__ __forceinline__ bool prim_of(const R q[5], R gm1, Prim<R>& p) {
+DG_HD bool prim_of(const R q[5], R gm1, Prim<R>& p) {
   const R ir = R(1) / q[0];
   p.rho = q[0];
   p.U = q[1] * ir;
@@ -93,18 +105,18 @@ __device__ __forceinline__ bool prim_of(const R q[5], R gm1, Prim<R>& p) {
 
 // ---- moments of products (compile-time powers) ----
 template <int A, int B, int C, class R>
-__device__ __forceinline__ R Gm(const MomTab<R>& t) {
+DG_HD R Gm(const MomTab<R>& t) {
   static_assert(A <= 6 && B <= 6 && C <= 6, "moment power out of table");
   return t.u[A] * t.v[B] * t.w[C];
 }
 // <u^A v^B w^C psi_5>
 template <int A, int B, int C, class R>
-__device__ __forceinline__ R G5(const MomTab<R>& t) {
+DG_HD R G5(const MomTab<R>& t) {
   return R(0.5) * (Gm<A + 2, B, C>(t) + Gm<A, B + 2, C>(t) + Gm<A, B, C + 2>(t) + t.xi2 * Gm<A, B, C>(t));
 }
 // <u^A v^B w^C psi_5^2>
 template <int A, int B, int C, class R>
-__device__ __forceinline__ R G55(const MomTab<R>& t) {
+DG_HD R G55(const MomTab<R>& t) {
   return R(0.25) * (Gm<A + 4, B, C>(t) + Gm<A, B + 4, C>(t) + Gm<A, B, C + 4>(t) +
                     R(2) * (Gm<A + 2, B + 2, C>(t) + Gm<A + 2, B, C + 2>(t) + Gm<A, B + 2, C + 2>(t)) +
                     R(2) * t.xi2 * (Gm<A + 2, B, C>(t) + Gm<A, B + 2, C>(t) + Gm<A, B, C + 2>(t)) +
@@ -113,7 +125,7 @@ __device__ __forceinline__ R G55(const MomTab<R>& t) {
 
 // out += s * <u^A v^B w^C psi>
 template <int A, int B, int C, class R>
-__device__ __forceinline__ void mom_psi(const MomTab<R>& t, R s, R out[5]) {
+DG_HD void mom_psi(const MomTab<R>& t, R s, R out[5]) {
   out[0] += s * Gm<A, B, C>(t);
   out[1] += s * Gm<A + 1, B, C>(t);
   out[2] += s * Gm<A, B + 1, C>(t);
@@ -123,7 +135,7 @@ __device__ __forceinline__ void mom_psi(const MomTab<R>& t, R s, R out[5]) {
 
 // out += s * <u^A v^B w^C (a . psi) psi>
 template <int A, int B, int C, class R>
-__device__ __forceinline__ void mom_a_psi(const MomTab<R>& t, const R a[5], R s, R out[5]) {
+DG_HD void mom_a_psi(const MomTab<R>& t, const R a[5], R s, R out[5]) {
   out[0] += s * (a[0] * Gm<A, B, C>(t) + a[1] * Gm<A + 1, B, C>(t) + a[2] * Gm<A, B + 1, C>(t) +
                  a[3] * Gm<A, B, C + 1>(t) + a[4] * G5<A, B, C>(t));
   out[1] += s * (a[0] * Gm<A + 1, B, C>(t) + a[1] * Gm<A + 2, B, C>(t) + a[2] * Gm<A + 1, B + 1, C>(t) +
@@ -138,7 +150,7 @@ __device__ __forceinline__ void mom_a_psi(const MomTab<R>& t, const R a[5], R s,
 
 // out += s * <u_D^(E) (a_x u + a_y v + a_z w) psi> with u_D^E = u^E (D=0), v^E (D=1), w^E (D=2)
 template <int D, int E, class R>
-__device__ __forceinline__ void mom_adotu_psi(const MomTab<R>& t, const R a[3][5], R s, R out[5]) {
+DG_HD void mom_adotu_psi(const MomTab<R>& t, const R a[3][5], R s, R out[5]) {
   constexpr int A = (D == 0) ? E : 0, B = (D == 1) ? E : 0, C = (D == 2) ? E : 0;
   mom_a_psi<A + 1, B, C>(t, a[0], s, out);
   mom_a_psi<A, B + 1, C>(t, a[1], s, out);
@@ -146,16 +158,16 @@ __device__ __forceinline__ void mom_adotu_psi(const MomTab<R>& t, const R a[3][5
 }
 
 template <int D, class R>
-__device__ __forceinline__ void mom_ud_psi(const MomTab<R>& t, R s, R out[5]) {
+DG_HD void mom_ud_psi(const MomTab<R>& t, R s, R out[5]) {
   mom_psi<(D == 0), (D == 1), (D == 2)>(t, s, out);
 }
 template <int D, class R>
-__device__ __forceinline__ void mom_ud_a_psi(const MomTab<R>& t, const R a[5], R s, R out[5]) {
+DG_HD void mom_ud_a_psi(const MomTab<R>& t, const R a[5], R s, R out[5]) {
   mom_a_psi<(D == 0), (D == 1), (D == 2)>(t, a, s, out);
 }
 
 template <class R>
-__device__ __forceinline__ void full_table(const Prim<R>& p, R K, MomTab<R>& t) {
+DG_HD void full_table(const Prim<R>& p, R K, MomTab<R>& t) {
   const R h = R(0.5) / p.lam;
   full_line(t.u, p.U, h);
   full_line(t.v, p.V, h);
@@ -169,7 +181,7 @@ __device__ __forceinline__ void full_table(const Prim<R>& p, R K, MomTab<R>& t) 
 // a_4 = 4 lam^2/(K+3) (2 b_4 - E b_0 - 2 U.r), a_i = 2 lam r_i - U_i a_4,
 // a_0 = b_0 - U.a_{1..3} - a_4 E / 2.
 template <class R>
-__device__ __forceinline__ void slope_solve(const Prim<R>& p, R K, const R b[5], R a[5]) {
+DG_HD void slope_solve(const Prim<R>& p, R K, const R b[5], R a[5]) {
   const R E = p.U * p.U + p.V * p.V + p.W * p.W + (K + R(3)) * R(0.5) / p.lam;
   const R r1 = b[1] - p.U * b[0], r2 = b[2] - p.V * b[0], r3 = b[3] - p.W * b[0];
   a[4] = R(4) * p.lam * p.lam / (K + R(3)) * (R(2) * b[4] - E * b[0] - R(2) * (p.U * r1 + p.V * r2 + p.W * r3));
@@ -183,7 +195,7 @@ __device__ __forceinline__ void slope_solve(const Prim<R>& p, R K, const R b[5],
 // heat-flux moment of one term phi: 1/2 <(u_n - U_n)(|u-U|^2 + xi^2) phi> from
 // F = <u_n psi phi>, W = <psi phi>; (U_n, Ut1, Ut2) = velocity, normal first.
 template <class R>
-__device__ __forceinline__ R heat_of(const R F[5], const R W[5], R Un, R Ut1, R Ut2, int n) {
+DG_HD R heat_of(const R F[5], const R W[5], R Un, R Ut1, R Ut2, int n) {
   // components of psi: 1 -> U_n is component 1+n in the frame where F was taken
   const R U2 = Un * Un + Ut1 * Ut1 + Ut2 * Ut2;
   (void)n;
@@ -198,7 +210,7 @@ __device__ __forceinline__ R heat_of(const R F[5], const R W[5], R Un, R Ut1, R 
 //   wF  = (1 - phi, 2 tau phi - tau (2 - s^2), tau phi - tau, phi, -2 tau phi + tau (1 - s^2), -tau phi)
 //   wFt = (q, -2 tau q + 4 x Eh s, 1 - tau q, -q, 2 tau q - 4 x Eh s, tau q)
 template <class R>
-__device__ __forceinline__ void fit_weights(R tau, R dt, R inv_dt, R wF[6], R wFt[6]) {
+DG_HD void fit_weights(R tau, R dt, R inv_dt, R wF[6], R wFt[6]) {
   R Eh = R(0), x = R(0);
   if (tau > R(0)) {
     Eh = exp(R(-0.5) * dt / tau);
@@ -235,7 +247,7 @@ struct SideSums {
 };
 
 template <class R, int SGN>
-__device__ __forceinline__ bool iface_side(const R q[5], const R dq[3][5], const GasPar<R>& g, bool pr_fix,
+DG_HD bool iface_side(const R q[5], const R dq[3][5], const GasPar<R>& g, bool pr_fix,
                                            SideSums<R>& S) {
   Prim<R> p;
   const bool ok = prim_of(q, g.gm1, p);
@@ -272,7 +284,7 @@ __device__ __forceinline__ bool iface_side(const R q[5], const R dq[3][5], const
 }
 
 template <class R>
-__device__ __forceinline__ bool iface_flux(const R qL[5], const R dqL[3][5], const R qR[5], const R dqR[3][5],
+DG_HD bool iface_flux(const R qL[5], const R dqL[3][5], const R qR[5], const R dqR[3][5],
                                            const GasPar<R>& g, R F[5], R Ft[5]) {
   const bool pr_fix = (g.pr_fix != R(0));
   SideSums<R> S;
@@ -346,7 +358,7 @@ __device__ __forceinline__ bool iface_flux(const R qL[5], const R dqL[3][5], con
 // Interior flux of Eq. (flux-2) in the global frame: F[d][k], Ft[d][k].
 // ---------------------------------------------------------------------------
 template <int D, class R>
-__device__ __forceinline__ void interior_dir(const MomTab<R>& t, const Prim<R>& p, const R a[3][5], const R A[5],
+DG_HD void interior_dir(const MomTab<R>& t, const Prim<R>& p, const R a[3][5], const R A[5],
                                              const R Wau[5], R tau, const GasPar<R>& g, R F[5], R Ft[5]) {
   R m0[5] = {R(0), R(0), R(0), R(0), R(0)}, m1[5] = {R(0), R(0), R(0), R(0), R(0)},
     m2[5] = {R(0), R(0), R(0), R(0), R(0)};
@@ -394,7 +406,7 @@ __device__ __forceinline__ void interior_dir(const MomTab<R>& t, const Prim<R>& 
 }
 
 template <class R>
-__device__ __forceinline__ bool interior_flux(const R q[5], const R dq[3][5], const GasPar<R>& g, R F[3][5],
+DG_HD bool interior_flux(const R q[5], const R dq[3][5], const GasPar<R>& g, R F[3][5],
                                               R Ft[3][5]) {
   Prim<R> p;
   const bool ok = prim_of(q, g.gm1, p);

@@ -1,0 +1,184 @@
+// Algorithmic operation counts of the DG-HGKS point computations.
+//
+// The device flux functions of gks_point.cuh are instantiated on the host
+// with a counting scalar: every distinct +, -, *, / between two values is one
+// floating-point operation (value numbering removes repeated subexpressions
+// and operations with constant 0 or +-1 operands), and sqrt, exp, erfc are
+// counted apart (they run on the special-function pipe and as
+// multi-instruction sequences).  The
+// trace evaluation (modal -> Gauss point values and gradients) and the
+// quadrature projections are counted from their loop structure, keeping
+// only terms whose basis factor is not identically zero.
+//
+// Output (stdout): one JSON object per (order, n_q, Pr != 1) with the counts
+// per face point and per cell point.  The benchmark divides the counted
+// operations of one launch by its measured duration for the roofline.
+#define DG_HD inline
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <tuple>
+#include <utility>
+
+namespace opc {
+// Value numbering: every distinct (operation, operands) pair is counted once,
+// as a compiler's common-subexpression elimination would; operations with a
+// constant 0 or +-1 operand are free (folded).
+struct Tally {
+  long add = 0, mul = 0, div = 0, sqrt = 0, exp = 0, erfc = 0;
+  long flops() const { return add + mul + div; }
+};
+Tally g;
+std::map<std::tuple<char, int, int>, int> memo;
+std::map<double, int> const_ids;
+std::map<int, double> const_vals;
+int next_id = 1;
+
+inline int const_id(double x) {
+  auto it = const_ids.find(x);
+  if (it != const_ids.end()) return it->second;
+  const int id = next_id++;
+  const_ids[x] = id;
+  const_vals[id] = x;
+  return id;
+}
+inline bool is_const(int id, double x) {
+  auto it = const_vals.find(id);
+  return it != const_vals.end() && it->second == x;
+}
+inline void reset() {
+  g = Tally();
+  memo.clear();
+}
+
+struct Cnt {
+  double v;
+  int id;
+  Cnt() : v(0), id(const_id(0.0)) {}
+  Cnt(double x) : v(x), id(const_id(x)) {}
+  Cnt(double x, int i) : v(x), id(i) {}
+};
+
+// returns the id of (op, a, b), counting it in *slot if it is new
+inline int vn(char op, int a, int b, long* slot) {
+  if (op == '+' || op == '*')
+    if (a > b) std::swap(a, b);
+  auto key = std::make_tuple(op, a, b);
+  auto it = memo.find(key);
+  if (it != memo.end()) return it->second;
+  if (slot) ++*slot;
+  const int id = next_id++;
+  memo[key] = id;
+  return id;
+}
+inline Cnt operator+(Cnt a, Cnt b) {
+  if (is_const(a.id, 0.0)) return b;
+  if (is_const(b.id, 0.0)) return a;
+  return Cnt(a.v + b.v, vn('+', a.id, b.id, &g.add));
+}
+inline Cnt operator-(Cnt a, Cnt b) {
+  if (is_const(b.id, 0.0)) return a;
+  return Cnt(a.v - b.v, vn('-', a.id, b.id, &g.add));
+}
+inline Cnt operator*(Cnt a, Cnt b) {
+  if (is_const(a.id, 0.0) || is_const(b.id, 0.0)) return Cnt(0.0);
+  if (is_const(a.id, 1.0)) return b;
+  if (is_const(b.id, 1.0)) return a;
+  if (is_const(a.id, -1.0)) return Cnt(-b.v, vn('n', b.id, 0, nullptr));
+  if (is_const(b.id, -1.0)) return Cnt(-a.v, vn('n', a.id, 0, nullptr));
+  return Cnt(a.v * b.v, vn('*', a.id, b.id, &g.mul));
+}
+inline Cnt operator/(Cnt a, Cnt b) {
+  if (is_const(b.id, 1.0)) return a;
+  return Cnt(a.v / b.v, vn('/', a.id, b.id, &g.div));
+}
+inline Cnt operator-(Cnt a) { return Cnt(-a.v, vn('n', a.id, 0, nullptr)); }
+inline Cnt& operator+=(Cnt& a, Cnt b) { a = a + b; return a; }
+inline bool operator>(Cnt a, Cnt b) { return a.v > b.v; }
+inline bool operator<(Cnt a, Cnt b) { return a.v < b.v; }
+inline bool operator!=(Cnt a, Cnt b) { return a.v != b.v; }
+inline Cnt sqrt(Cnt a) { return Cnt(std::sqrt(a.v), vn('s', a.id, 0, &g.sqrt)); }
+inline Cnt exp(Cnt a) { return Cnt(std::exp(a.v), vn('e', a.id, 0, &g.exp)); }
+inline Cnt erfc(Cnt a) { return Cnt(std::erfc(a.v), vn('c', a.id, 0, &g.erfc)); }
+}  // namespace opc
+
+#include "gks_point.cuh"
+
+using opc::Cnt;
+using namespace dghgks;
+
+static int n_modes_(int k) { return (k + 1) * (k + 2) * (k + 3) / 6; }
+static int n_tmodes_(int k) { return (k + 1) * (k + 2) / 2; }
+
+// number of modes of P_k with a non-zero derivative along one axis
+static int n_modes_dx(int k) {
+  int c = 0;
+  for (int a = 0; a <= k; ++a)
+    for (int b = 0; a + b <= k; ++b)
+      for (int d = 0; a + b + d <= k; ++d)
+        if (a > 0) ++c;
+  return c;
+}
+
+static void state(Cnt q[5], Cnt dq[3][5], double s) {
+  const double rho = 1.1 + 0.1 * s, U = 0.3, V = -0.2, W = 0.1 * s, p = 71.4;
+  q[0] = rho;
+  q[1] = rho * U;
+  q[2] = rho * V;
+  q[3] = rho * W;
+  q[4] = p / 0.4 + 0.5 * rho * (U * U + V * V + W * W);
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 5; ++k) dq[i][k] = 0.01 * (1 + i + k) * (k == 4 ? 100.0 : 1.0);
+}
+
+static void emit(int order, int nq, double pr) {
+  GasPar<Cnt> gp;
+  gp.K = 2.0;
+  gp.gm1 = 0.4;
+  gp.mu = 1.0 / 1600;
+  gp.tau_add = 0.0;
+  gp.pr_fix = 1.0 / pr - 1.0;
+  gp.dt = 3.3e-4;
+  gp.inv_dt = 1.0 / 3.3e-4;
+  Cnt qL[5], dqL[3][5], qR[5], dqR[3][5], F[5], Ft[5], Fc[3][5], Ftc[3][5];
+  state(qL, dqL, 0.0);
+  state(qR, dqR, 1.0);
+  opc::reset();
+  iface_flux(qL, dqL, qR, dqR, gp, F, Ft);
+  const opc::Tally face = opc::g;
+  opc::reset();
+  interior_flux(qL, dqL, gp, Fc, Ftc);
+  const opc::Tally cell = opc::g;
+
+  const int NM = n_modes_(order), NT = n_tmodes_(order), NMx = n_modes_dx(order);
+  // traces, per side (face) or per point (cell): per mode the basis products
+  // (value 2, three gradients 2 each -> 8 multiplies; on a face the normal
+  // factor is a constant +-1 or n(n+1)/2, so 5), then 4 FMAs (8 flops) per
+  // variable, then 3 x 5 gradient scalings by 2/h.
+  const long trace_face_side = NM * 5 + NM * 5 * 8 + 15;
+  const long trace_cell = NM * 8 + NM * 5 * 8 + 15;
+  // face projection per point: 10 components x NT tangential modes FMA,
+  // plus 10 weight multiplies
+  const long proj_face = 10 * NT * 2 + 10;
+  // cell projection per point: per direction only the NMx modes with a
+  // non-zero derivative, 5 variables x (F, F_t) FMAs; plus 30 weight multiplies
+  const long proj_cell = 3 * NMx * 5 * 2 * 2 + 30;
+  const long face_total = face.flops() + 2 * trace_face_side + proj_face;
+  const long cell_total = cell.flops() + trace_cell + proj_cell;
+  printf(
+      "{\"order\": %d, \"n_q\": %d, \"pr_fix\": %s, "
+      "\"face_point\": {\"flux_flops\": %ld, \"div\": %ld, \"sqrt\": %ld, \"exp\": %ld, \"erfc\": %ld, "
+      "\"trace_flops\": %ld, \"proj_flops\": %ld, \"total_flops\": %ld}, "
+      "\"cell_point\": {\"flux_flops\": %ld, \"div\": %ld, \"sqrt\": %ld, \"exp\": %ld, \"erfc\": %ld, "
+      "\"trace_flops\": %ld, \"proj_flops\": %ld, \"total_flops\": %ld}}\n",
+      order, nq, pr != 1.0 ? "true" : "false", face.flops(), face.div, face.sqrt, face.exp, face.erfc,
+      2 * trace_face_side, proj_face, face_total, cell.flops(), cell.div, cell.sqrt, cell.exp, cell.erfc, trace_cell,
+      proj_cell, cell_total);
+}
+
+int main() {
+  const int cfg[][2] = {{1, 2}, {2, 2}, {2, 3}, {3, 3}, {3, 4}};
+  for (auto& c : cfg)
+    for (double pr : {1.0, 0.72}) emit(c[0], c[1], pr);
+  return 0;
+}

@@ -1,12 +1,18 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerance (FP64 path): for each output array (L, L_t, or a state increment)
-and each variable v, max |gpu - oracle| <= 1e-11 * max |oracle| over all cells
-and modes of that variable.  The two sides evaluate the same formulas in a
-different order (closed-form vs LU slope solves, compile-time moment
-products vs expanded monomials, CUDA vs glibc exp/erfc), so they agree to
-rounding amplified by the cancellations of the method (pressure fluxes that
-cancel across a cell, equilibrium minus free-transport terms of d_t F).
+Tolerance (FP64 path), relative 1e-11 per variable:
+  * residuals L, L_t: max |gpu - oracle| <= 1e-11 * S_v, where S_v is the
+    largest coefficient of variable v of M^-1 sum |contribution| (the oracle's
+    absolute-value residual, the scale of the summands).  The residual is a sum
+    with heavy cancellation: in the low-Mach Taylor-Green flow the pressure
+    fluxes (~p0 = 71) of opposite faces cancel to O(1), and the cancellation
+    grows like 1/h, so two FP64 evaluations that differ only in operation
+    order (closed-form vs LU slope solves, compile-time moment products vs
+    expanded monomials, CUDA vs glibc exp/erfc) agree to ~eps * S_v, not to
+    ~eps * |L|.  The result-relative error max|gpu - oracle| / max|oracle| is
+    also asserted below 1e-11 on the grids up to 37 cells wide.
+  * S2O4 state increments Q^{n+2} - Q^n: max |gpu - oracle| <= 1e-11 * max
+    |oracle increment| per variable.
 """
 import math
 
@@ -50,13 +56,28 @@ def make(api, orc, n, lo, hi, order, nq, mu=0.0, Pr=1.0, tau_eps=0.0, precision=
     return s, pb
 
 
+def oracle_residual(orc, pb, Q, dt):
+    """Oracle (L, L_t, A, A_t) in the state layout."""
+    nc = int(np.prod(pb.n))
+    out = orc.residual_cells(pb, Q, dt, np.arange(nc), scales=True)
+    return [x.transpose(1, 2, 0).reshape(pb.shape) for x in out]
+
+
+def assert_residual_parity(L, Lt, ref):
+    Lo, Lto, A, At = ref
+    for a, b, sc in ((L, Lo, A), (Lt, Lto, At)):
+        err = np.abs(a - b).reshape(5, -1).max(axis=1)
+        scale = np.abs(sc).reshape(5, -1).max(axis=1)
+        assert np.all(err <= RTOL * scale), (err / scale)
+        assert per_var_err(a, b).max() < RTOL
+
+
 def residual_pair(torch, s, pb, orc, Q, dt):
     Qd = torch.from_numpy(Q).cuda()
     L, Lt = s.residual(Qd, dt)
     torch.cuda.synchronize()
     s.status()
-    Lo, Lto = orc.residual(pb, Q, dt)
-    return L.cpu().numpy(), Lt.cpu().numpy(), Lo, Lto
+    return L.cpu().numpy(), Lt.cpu().numpy(), oracle_residual(orc, pb, Q, dt)
 
 
 ADV = dict(lo=(0.0,) * 3, hi=(2.0,) * 3)
@@ -69,9 +90,8 @@ def test_advection_p1_residual(torch, api, orc, n):
 
     s, pb = make(api, orc, n, order=1, nq=2, tau_eps=0.01, **ADV)
     Q = inputs.modal_state(inputs.advection_prim, n, 1, ADV["lo"], ADV["hi"], perturb=1e-3)
-    L, Lt, Lo, Lto = residual_pair(torch, s, pb, orc, Q, 8.2e-3)
-    assert per_var_err(L, Lo).max() < RTOL
-    assert per_var_err(Lt, Lto).max() < RTOL
+    L, Lt, ref = residual_pair(torch, s, pb, orc, Q, 8.2e-3)
+    assert_residual_parity(L, Lt, ref)
 
 
 @pytest.mark.parametrize("nq", [3, 2])
@@ -83,9 +103,8 @@ def test_tgv_p2_residual(torch, api, orc, n, Pr, nq):
     s, pb = make(api, orc, n, order=2, nq=nq, mu=1 / 1600, Pr=Pr, **TGV)
     Q = inputs.modal_state(inputs.tgv_prim, n, 2, TGV["lo"], TGV["hi"], perturb=1e-3)
     dt = 1.3e-3
-    L, Lt, Lo, Lto = residual_pair(torch, s, pb, orc, Q, dt)
-    assert per_var_err(L, Lo).max() < RTOL
-    assert per_var_err(Lt, Lto).max() < RTOL
+    L, Lt, ref = residual_pair(torch, s, pb, orc, Q, dt)
+    assert_residual_parity(L, Lt, ref)
 
 
 @pytest.mark.parametrize("order,nq", [(1, 2), (2, 3), (2, 2)])
@@ -96,9 +115,8 @@ def test_random_discontinuous_states(torch, api, orc, order, nq, mu, tau_eps, Pr
     n = (5, 4, 3)
     s, pb = make(api, orc, n, lo=(0, 0, 0), hi=(1.0, 0.8, 0.6), order=order, nq=nq, mu=mu, Pr=Pr, tau_eps=tau_eps)
     Q = inputs.random_state(n, order, seed=7 + order)
-    L, Lt, Lo, Lto = residual_pair(torch, s, pb, orc, Q, 2e-3)
-    assert per_var_err(L, Lo).max() < RTOL
-    assert per_var_err(Lt, Lto).max() < RTOL
+    L, Lt, ref = residual_pair(torch, s, pb, orc, Q, 2e-3)
+    assert_residual_parity(L, Lt, ref)
 
 
 @pytest.mark.parametrize("order,nq,case", [(1, 2, "adv"), (2, 3, "tgv")])
@@ -129,23 +147,23 @@ def test_sampled_cells_full_size_tgv_256(torch, api, orc):
 
     n = (256, 256, 256)
     s, pb = make(api, orc, n, order=2, nq=3, mu=1 / 1600, Pr=0.72, **TGV)
-    Q = inputs.tgv_state(256, 2)
+    Qd = inputs.tgv_state(256, 2, device="cuda")
+    Q = Qd.cpu().numpy()
     dt = inputs.tgv_dt(256, 2)
-    Qd = torch.from_numpy(Q).cuda()
     L, Lt = s.residual(Qd, dt)
     torch.cuda.synchronize()
     s.status()
     rng = np.random.default_rng(0)
     cells = np.concatenate([[0, 255, 256 * 256 - 1, 256 ** 3 - 1, 256 * 255 + 31, 256 * 256 * 128 + 33],
                             rng.integers(0, 256 ** 3, 40)])
-    Lo, Lto = orc.residual_cells(pb, Q, dt, cells)
+    Lo, Lto, Ao, Ato = orc.residual_cells(pb, Q, dt, cells, scales=True)
     Lc = L.reshape(5, 10, -1)[:, :, cells].permute(2, 0, 1).cpu().numpy()
     Ltc = Lt.reshape(5, 10, -1)[:, :, cells].permute(2, 0, 1).cpu().numpy()
     # scale per variable over the sampled cells
-    for A, B in ((Lc, Lo), (Ltc, Lto)):
-        scale = np.abs(B).max(axis=(0, 2))
-        err = np.abs(A - B).max(axis=(0, 2)) / scale
-        assert err.max() < RTOL, err
+    for a, b, sc in ((Lc, Lo, Ao), (Ltc, Lto, Ato)):
+        err = np.abs(a - b).max(axis=(0, 2))
+        scale = np.abs(sc).max(axis=(0, 2))
+        assert np.all(err <= RTOL * scale), err / scale
 
 
 def test_totals_and_kinetic_energy(torch, api, orc):
