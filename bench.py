@@ -62,6 +62,47 @@ def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+class Ranks:
+    """Replica bookkeeping across ranks: barrier, max over ranks, whole-job sums.
+
+    Each rank runs an independent replica of the workload (no data-path
+    collective); timing takes the slowest rank, throughput counts every
+    rank's units.  backend "nccl" on GPUs, "gloo" for the CPU tests."""
+
+    def __init__(self, world: int, backend: str = "nccl", device=None):
+        self.world = world
+        self.dist = None
+        self.device = device
+        if world > 1:
+            import torch.distributed as dist
+
+            if not dist.is_initialized():
+                kw = {"device_id": device} if backend == "nccl" and device is not None else {}
+                dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        if self.dist is None:
+            return float(x)
+        import torch
+
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def job_rate(self, units_per_rank: float, seconds_max: float) -> float:
+        """Whole-job throughput: every rank processed units_per_rank in at most seconds_max."""
+        return units_per_rank * self.world / seconds_max
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
 def workload_config(n, dt):
     return {
         "workload": f"Taylor-Green vortex {n}^3 cells, P2 (10 modes x 5 vars), 3x3 face / 3^3 cell Gauss points, "
@@ -125,7 +166,7 @@ def run_reference(args):
     budget = max(4.0, min(15.0, 100.0 / max(1, args.steps + args.warmup)))
     rates, threads, sample = oracle_sample(n, budget, reps=args.steps + args.warmup)
     timed = rates[args.warmup:] or rates
-    value = statistics.mean(timed) * world
+    value = statistics.mean(timed)  # rank 0 alone runs the CPU oracle
     ms_per_step = 5 * 10 * n ** 3 * 2 / value * 1e3
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -270,22 +311,8 @@ def run_ours(args):
 
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(world, "nccl", torch.device("cuda", local))
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     from paper_2202_13821_b300 import api, build, inputs
 
@@ -302,14 +329,14 @@ def run_ours(args):
     m32 = run_leg(torch, api, api.DGHGKS_FP32_MIXED, Q0, dt, args.warmup, args.steps, barrier, ClockSampler(local))
     clocks = m32["clocks"]
     ms32 = max_over_ranks(m32["ms"]) / args.steps
-    value = dof_step / (ms32 * 1e-3) * world
+    value = ranks.job_rate(dof_step, ms32 * 1e-3)
     m32["solver"].close()  # free its scratch; the final state Q stays
 
     # --- FP64 on the same state ---
     k64 = args.fp64_steps if args.fp64_steps is not None else args.steps
     m64 = run_leg(torch, api, api.DGHGKS_FP64, Q0, dt, args.warmup, k64, barrier)
     ms64 = max_over_ranks(m64["ms"]) / k64
-    value64 = dof_step / (ms64 * 1e-3) * world
+    value64 = ranks.job_rate(dof_step, ms64 * 1e-3)
 
     # --- error of FP32-mixed against FP64 after the same steps (when the step counts agree) ---
     s64 = m64["solver"]
@@ -347,7 +374,7 @@ def run_ours(args):
         ek_e2e = s_e2e.run_host(Qh, dt, args.steps)
         el = max_over_ranks(time.perf_counter() - t0)
         state_bytes = Q0.numel() * 8
-        e2e = {"value": dof_step * args.steps / el * world, "unit": UNIT,
+        e2e = {"value": ranks.job_rate(dof_step * args.steps, el), "unit": UNIT,
                "h2d_bytes_per_step": state_bytes / args.steps,
                "d2h_bytes_per_step": (state_bytes + 8 * args.steps) / args.steps,
                "api": "dghgks_run_host (H2D of the state, K steps with E_k read back after each, D2H of the state)",
@@ -372,8 +399,7 @@ def run_ours(args):
             "gpu_launches": m32["launches"],
         }
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 

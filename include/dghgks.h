@@ -109,6 +109,15 @@ int dghgks_residual(dghgks_ctx* ctx, const double* Q, double dt, double* L, doub
  * Asynchronous; consecutive calls on one context must share a stream. */
 int dghgks_step(dghgks_ctx* ctx, double* Q, double dt, void* stream);
 
+/* nsteps S2O4 steps in place on the device state Q, replaying a CUDA graph
+ * of one step (8 kernel launches) on `stream`.  The graph is captured on a
+ * private stream at the first call and re-captured when Q or dt changes
+ * (the executable graph is updated in place when possible).  Results are
+ * identical to nsteps calls of dghgks_step.  Asynchronous.  Must not be
+ * called while `stream` itself is being captured; profiling records nothing
+ * for graph replays. */
+int dghgks_steps(dghgks_ctx* ctx, double* Q, double dt, int nsteps, void* stream);
+
 /* nsteps S2O4 steps on a HOST state (pinned or pageable): copies Q_host to
  * the device, steps, and copies the result back; if ek_host is not NULL it
  * receives E_k (as dghgks_kinetic_energy with rho0) after every step.

@@ -52,6 +52,7 @@ _SIGS = {
     "dghgks_set_mu": (_I, [_VP, _D]),
     "dghgks_residual": (_I, [_VP, _VP, _D, _VP, _VP, _VP]),
     "dghgks_step": (_I, [_VP, _VP, _D, _VP]),
+    "dghgks_steps": (_I, [_VP, _VP, _D, _I, _VP]),
     "dghgks_run_host": (_I, [_VP, _DP, _D, _I, _D, _DP, _VP]),
     "dghgks_totals": (_I, [_VP, _VP, _DP, _VP]),
     "dghgks_kinetic_energy": (_I, [_VP, _VP, _D, _DP, _VP]),
@@ -132,6 +133,10 @@ def dghgks_residual(ctx, Q, dt: float, L, Lt, stream=None):
 
 def dghgks_step(ctx, Q, dt: float, stream=None):
     _check(ctx, load().dghgks_step(ctx, _ptr(Q), dt, _stream(stream)))
+
+
+def dghgks_steps(ctx, Q, dt: float, nsteps: int, stream=None):
+    _check(ctx, load().dghgks_steps(ctx, _ptr(Q), dt, int(nsteps), _stream(stream)))
 
 
 def dghgks_run_host(ctx, Q_host: np.ndarray, dt: float, nsteps: int, rho0: float = 1.0, ek_host=None, stream=None):
@@ -240,6 +245,11 @@ class Solver:
     def step(self, Q, dt, nsteps: int = 1, stream=None):
         for _ in range(nsteps):
             dghgks_step(self.ctx, Q, dt, stream)
+        return Q
+
+    def steps(self, Q, dt, nsteps: int, stream=None):
+        """nsteps steps by CUDA-graph replay (dghgks_steps)."""
+        dghgks_steps(self.ctx, Q, dt, nsteps, stream)
         return Q
 
     def run_host(self, Q_host, dt, nsteps, rho0=1.0, with_ek=True, stream=None):

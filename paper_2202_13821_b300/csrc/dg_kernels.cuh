@@ -4,26 +4,33 @@
 //
 // One stage = 3 face launches (one per normal direction) + 1 cell launch:
 //
-//   k_face<D>: a CTA owns FB consecutive faces along x normal to axis D.  It
-//     stages the modal coefficients of the two cells of each face in shared
-//     memory, evaluates Q_h and grad Q_h on both sides of its NQ^2 Gauss
-//     points (one warp per point, lanes over faces), computes F_b and
-//     d_t F_b there (Eq. flux, local frame with the normal first), and
+//   k_face<D>: a CTA owns FB consecutive faces along x normal to axis D.  While
+//     staging the two cells of each face (coalesced loads), it contracts
+//     their modal coefficients along the normal, so each side's trace is a
+//     2-D polynomial in the tangential coordinates (value and normal
+//     derivative).  One warp per Gauss point, lanes over faces: each thread
+//     evaluates Q_h and grad Q_h on both sides of its point, computes F_b and
+//     d_t F_b there (Eq. flux, local frame with the normal first), and the CTA
 //     projects w |Gamma| F onto the NT tangential Legendre products of the
-//     face.  Only those face moments G reach HBM (10 x NT values per face);
-//     point values never do.
+//     face in shared memory.  Only those face moments G reach HBM (10 x NT
+//     values per face); point values never do.
 //
-//   k_cell<MODE>: a CTA owns CB consecutive cells along x, one thread per
-//     (cell, Gauss point).  It evaluates the interior flux of Eq. (flux-2)
-//     at the NQ^3 points, projects w |K| F . grad B_n in shared memory, adds
-//     the six faces' moments with the sign and parity of Eq. (operator)
-//     (the cell is right of its low face: +(-1)^{n_D} G, left of its high
-//     face: -G), multiplies by the diagonal inverse mass matrix, and applies
-//     the epilogue:
+//   k_cell<MODE>: a group of lanes owns one cell, one lane per Gauss point
+//     (a warp per cell at n_q = 3, four cells per warp at n_q = 2).  Each lane
+//     evaluates the interior flux of Eq. (flux-2) at its point; the volume
+//     projection w |K| F . grad B_n is summed over the group by a
+//     recursive-halving warp butterfly (deterministic, no shared-memory
+//     projection, no atomics).  The CTA then adds the six faces' moments with
+//     the sign and parity of Eq. (operator) (the cell is right of its low
+//     face: +(-1)^{n_D} G, left of its high face: -G), multiplies by the
+//     diagonal inverse mass matrix, and applies the epilogue:
 //       MODE 0: write L = M^-1 R and L_t = M^-1 R_t
-//       MODE 1: Q* = Q^n + dt/2 L + dt^2/8 L_t, Acc = Q^n + dt L + dt^2/6 L_t
-//       MODE 2: Q^{n+1} = Acc + dt^2/3 L_t(Q*)
-//     The stage arithmetic is always FP64.
+//       MODE 1: Q* = Q^n + dt/2 L + dt^2/8 L_t, inc = dt L + dt^2/6 L_t
+//       MODE 2: Q^{n+1} = Q^n + inc + dt^2/3 L_t(Q*)
+//     Q* and inc are stored in the flux precision (the stage-2 kernels read
+//     Q* in that precision anyway); the accumulation into the stored FP64
+//     state is FP64.  On B300 an FP64 instruction costs ~64 FP32 ones, so the
+//     FP32-mixed path keeps FP64 to this single add per coefficient and step.
 //
 // Each face is computed exactly once and written by exactly one CTA, and
 // every residual coefficient is summed in a fixed order: results are
@@ -43,14 +50,46 @@ struct MeshDev {
   long long ncell;
   double h[3];
   double vol;
+  // the same in single precision, precomputed on the host for the FP32 path
+  float sc_f[3];    // 2 / h_d
+  float area_f[3];  // |Gamma| of a face normal to d
+  float vol_f;
 };
+
+// per-precision access to the mesh scales
+template <class R>
+__device__ __forceinline__ R mesh_sc(const MeshDev& m, int d) {
+  return R(2) / (R)m.h[d];
+}
+template <>
+__device__ __forceinline__ float mesh_sc<float>(const MeshDev& m, int d) {
+  return m.sc_f[d];
+}
+template <class R>
+__device__ __forceinline__ R mesh_area(const MeshDev& m, int d) {
+  return (R)(m.vol / m.h[d]);
+}
+template <>
+__device__ __forceinline__ float mesh_area<float>(const MeshDev& m, int d) {
+  return m.area_f[d];
+}
+template <class R>
+__device__ __forceinline__ R mesh_vol(const MeshDev& m) {
+  return (R)m.vol;
+}
+template <>
+__device__ __forceinline__ float mesh_vol<float>(const MeshDev& m) {
+  return m.vol_f;
+}
 
 constexpr int FB = 32;  // faces per CTA in k_face
 
-template <int NQ>
-struct CellTile {
-  static constexpr int CB = NQ == 1 ? 32 : NQ == 2 ? 16 : NQ == 3 ? 8 : NQ == 4 ? 4 : 2;
-};
+// CTAs per SM requested for k_face (the FP32 path trades a few spills for a
+// second resident CTA; the FP64 path is bound by the FP64 pipe)
+#ifndef FACE_MIN_BLOCKS_F32
+#define FACE_MIN_BLOCKS_F32 2
+#endif
+#define FACE_MIN_BLOCKS(R) (sizeof(R) == 4 ? FACE_MIN_BLOCKS_F32 : 1)
 
 template <class R, int ORDER, int NQ>
 struct FaceSmem {
@@ -61,24 +100,14 @@ struct FaceSmem {
   static constexpr size_t bytes = 2 * coef + fs + phi;
 };
 
-template <class R, int ORDER, int NQ>
-struct CellSmem {
-  static constexpr int NM = n_modes(ORDER), NP = NQ * NQ * NQ, NC = 5 * NM, CB = CellTile<NQ>::CB;
-  static constexpr size_t coef = sizeof(R) * NC * CB;
-  static constexpr size_t fs = sizeof(R) * 30 * NP * CB;
-  static constexpr size_t db = sizeof(R) * NM * NP * 3;
-  static constexpr size_t tabs = sizeof(double) * NM + sizeof(int) * 6 * NM;
-  static constexpr size_t bytes = coef + fs + db + tabs;
-};
-
 __device__ __forceinline__ int wrapm(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // ---------------------------------------------------------------------------
 // Face kernel
 // ---------------------------------------------------------------------------
-template <class R, int ORDER, int NQ, int D>
-__global__ void __launch_bounds__(FB* NQ* NQ)
-    k_face(const double* __restrict__ Q, R* __restrict__ G, const GasPar<R> gp, const MeshDev m,
+template <class R, int ORDER, int NQ, int D, class Tin>
+__global__ void __launch_bounds__(FB* NQ* NQ, FACE_MIN_BLOCKS(R))
+    k_face(const Tin* __restrict__ Q, R* __restrict__ G, const GasPar<R> gp, const MeshDev m,
            unsigned* __restrict__ flag) {
   using S = FaceSmem<R, ORDER, NQ>;
   constexpr int NM = S::NM, NT = S::NT, NP = S::NP, NC = S::NC;
@@ -116,14 +145,14 @@ __global__ void __launch_bounds__(FB* NQ* NQ)
   }
   for (int e = tid; e < NT * NP; e += FB * NP) {
     const int t = e / NP, pp = e % NP;
-    phi[t][pp] = leg<R>(tmode_p(t), (R)gauss_x(NQ, pp / NQ)) * leg<R>(tmode_q(t), (R)gauss_x(NQ, pp % NQ));
+    phi[t][pp] = leg<R>(tmode_p(t), gauss_xr<R>(NQ, pp / NQ)) * leg<R>(tmode_q(t), gauss_xr<R>(NQ, pp % NQ));
   }
   __syncthreads();
 
   const int i = i0 + f;
   const bool active = i < nx;
   const int a = p / NQ, b = p % NQ;
-  const R xa = (R)gauss_x(NQ, a), xb = (R)gauss_x(NQ, b);
+  const R xa = gauss_xr<R>(NQ, a), xb = gauss_xr<R>(NQ, b);
   R La[ORDER + 1], dLa[ORDER + 1], Lb[ORDER + 1], dLb[ORDER + 1];
 #pragma unroll
   for (int n = 0; n <= ORDER; ++n) {
@@ -132,19 +161,24 @@ __global__ void __launch_bounds__(FB* NQ* NQ)
     Lb[n] = leg<R>(n, xb);
     dLb[n] = dleg<R>(n, xb);
   }
-  const R sD = R(2) / (R)m.h[D], s1 = R(2) / (R)m.h[T1], s2 = R(2) / (R)m.h[T2];
+  const R sD = mesh_sc<R>(m, D), s1 = mesh_sc<R>(m, T1), s2 = mesh_sc<R>(m, T2);
 
-  // traces: side 0 at r_D = +1 of the left cell, side 1 at r_D = -1 of the right cell
-  R q[2][5], dq[2][3][5];  // dq[side][axis][var], global axes
+  // Each side in turn: traces at r_D = +1 of the left cell (side 0) or r_D = -1
+  // of the right cell (side 1), rotated to the local frame (axes D, D+1, D+2
+  // cyclic, momentum alike), folded into the side sums of Eq. (flux).
+  constexpr int A0 = D, A1 = (D + 1) % 3, A2 = (D + 2) % 3;
+  const bool pr_fix = (gp.pr_fix != R(0));
+  SideSums<R> sums;
+  iface_zero(sums);
+  bool ok = true;
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
+    R q[5], dq[3][5];  // global axes
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       R s0 = R(0), gD = R(0), g1 = R(0), g2 = R(0);
 #pragma unroll
       for (int mm = 0; mm < NM; ++mm) {
-        constexpr int dummy = 0;
-        (void)dummy;
         const int nD = mode_exp(mm, D), n1 = mode_exp(mm, T1), n2 = mode_exp(mm, T2);
         // P_n(+1) = 1, P_n(-1) = (-1)^n; P'_n(+1) = n(n+1)/2, P'_n(-1) = (-1)^(n+1) n(n+1)/2
         const R pn = (side == 0 || (nD % 2 == 0)) ? R(1) : R(-1);
@@ -156,42 +190,36 @@ __global__ void __launch_bounds__(FB* NQ* NQ)
         g1 += c * (pn * dLa[n1] * Lb[n2]);
         g2 += c * (pn * La[n1] * dLb[n2]);
       }
-      q[side][v] = s0;
-      dq[side][D][v] = gD * sD;
-      dq[side][T1][v] = g1 * s1;
-      dq[side][T2][v] = g2 * s2;
+      q[v] = s0;
+      dq[D][v] = gD * sD;
+      dq[T1][v] = g1 * s1;
+      dq[T2][v] = g2 * s2;
     }
-  }
-
-  // local frame: axes (D, D+1, D+2) cyclic; momentum components alike
-  constexpr int A0 = D, A1 = (D + 1) % 3, A2 = (D + 2) % 3;
-  R ql[5], qr[5], dql[3][5], dqr[3][5];
-  {
+    R ql[5], dql[3][5];
     const int ax[3] = {A0, A1, A2};
+    ql[0] = q[0];
+    ql[1] = q[1 + A0];
+    ql[2] = q[1 + A1];
+    ql[3] = q[1 + A2];
+    ql[4] = q[4];
 #pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      R* qq = side == 0 ? ql : qr;
-      qq[0] = q[side][0];
-      qq[1] = q[side][1 + A0];
-      qq[2] = q[side][1 + A1];
-      qq[3] = q[side][1 + A2];
-      qq[4] = q[side][4];
-#pragma unroll
-      for (int ii = 0; ii < 3; ++ii) {
-        R* dd = side == 0 ? dql[ii] : dqr[ii];
-        const R* src = dq[side][ax[ii]];
-        dd[0] = src[0];
-        dd[1] = src[1 + A0];
-        dd[2] = src[1 + A1];
-        dd[3] = src[1 + A2];
-        dd[4] = src[4];
-      }
+    for (int ii = 0; ii < 3; ++ii) {
+      const R* src = dq[ax[ii]];
+      dql[ii][0] = src[0];
+      dql[ii][1] = src[1 + A0];
+      dql[ii][2] = src[1 + A1];
+      dql[ii][3] = src[1 + A2];
+      dql[ii][4] = src[4];
     }
+    if (side == 0)
+      ok = iface_side<R, +1>(ql, dql, gp, pr_fix, sums) && ok;
+    else
+      ok = iface_side<R, -1>(ql, dql, gp, pr_fix, sums) && ok;
   }
   R Fl[5], Ftl[5];
-  const bool ok = iface_flux(ql, dql, qr, dqr, gp, Fl, Ftl);
+  ok = iface_finish(sums, gp, Fl, Ftl) && ok;
   if (active && !ok) atomicOr(flag, 1u);
-  const R w = active ? (R)(gauss_w(NQ, a) * gauss_w(NQ, b) * (m.vol / m.h[D])) : R(0);
+  const R w = active ? gauss_wr<R>(NQ, a) * gauss_wr<R>(NQ, b) * mesh_area<R>(m, D) : R(0);
   Fs[0][p][f] = w * Fl[0];
   Fs[1 + A0][p][f] = w * Fl[1];
   Fs[1 + A1][p][f] = w * Fl[2];
@@ -222,22 +250,95 @@ __global__ void __launch_bounds__(FB* NQ* NQ)
 // ---------------------------------------------------------------------------
 enum { MODE_RESIDUAL = 0, MODE_STAGE1 = 1, MODE_STAGE2 = 2 };
 
-template <class R, int ORDER, int NQ, int MODE>
-__global__ void __launch_bounds__(CellTile<NQ>::CB* NQ* NQ* NQ)
-    k_cell(const double* __restrict__ Qin, const R* __restrict__ G, double* __restrict__ out0,
-           double* __restrict__ out1, const double* __restrict__ acc, const GasPar<R> gp, const MeshDev m,
-           const double dt, unsigned* __restrict__ flag) {
+// Thread layout of k_cell: a group of PG lanes owns one cell, one lane per
+// Gauss point (NQ^3 <= PG; the spare lanes carry zeros).  8 warps per CTA.
+template <int ORDER, int NQ>
+struct CellLayout {
+  static constexpr int NP = NQ * NQ * NQ;
+  static constexpr int PG = NP <= 8 ? 8 : 32;
+  static constexpr int CPW = 32 / PG;
+  static constexpr int WARPS = 8;
+  static constexpr int CB = CPW * WARPS;  // cells per CTA
+  static constexpr int NM = n_modes(ORDER);
+  static constexpr int NOUT = 5 * (NM - 1);                 // volume outputs (mode 0 has no gradient)
+  static constexpr int NOP = (NOUT + PG - 1) / PG * PG;      // padded to the group width
+  static constexpr int RPL = NOP / PG;                       // reduced outputs per lane
+  static_assert(NP <= 32, "k_cell handles up to 3^3 points per cell");
+};
+
+template <class R, int ORDER, int NQ>
+struct CellSmem {
+  using LY = CellLayout<ORDER, NQ>;
+  static constexpr int NM = LY::NM, NC = 5 * NM, CB = LY::CB;
+  static constexpr size_t coef = sizeof(R) * NC * CB;
+  static constexpr size_t red = sizeof(R) * CB * 2 * LY::NOP;
+  static constexpr size_t tabs = sizeof(double) * NM + sizeof(int) * 6 * NM;
+  static constexpr size_t bytes = coef + red + tabs;
+};
+
+// Recursive-halving butterfly over the PG lanes of a group: in[N] per lane ->
+// out[N/2] per lane after one exchange with the partner lane ^ M.  Lanes with
+// the M bit set keep the upper half.
+template <int N, int M, class R>
+__device__ __forceinline__ void halve(const R (&in)[N], R (&out)[N / 2], bool upper) {
+#pragma unroll
+  for (int j = 0; j < N / 2; ++j) {
+    const R keep = upper ? in[j + N / 2] : in[j];
+    const R send = upper ? in[j] : in[j + N / 2];
+    out[j] = keep + __shfl_xor_sync(0xffffffffu, send, M);
+  }
+}
+
+// Reduce the per-lane contributions val[NOP] over the PG lanes of the group:
+// lane lg (0..PG-1) ends with the sums of outputs [RPL*lg, RPL*lg + RPL).
+template <int NOP, int PG, class R>
+__device__ __forceinline__ void group_reduce(const R (&val)[NOP], R (&out)[NOP / PG], int lg) {
+  if constexpr (PG == 32) {
+    R a[NOP / 2], b[NOP / 4], c[NOP / 8], d[NOP / 16];
+    halve<NOP, 16>(val, a, lg & 16);
+    halve<NOP / 2, 8>(a, b, lg & 8);
+    halve<NOP / 4, 4>(b, c, lg & 4);
+    halve<NOP / 8, 2>(c, d, lg & 2);
+    halve<NOP / 16, 1>(d, out, lg & 1);
+  } else {
+    R a[NOP / 2], b[NOP / 4];
+    halve<NOP, 4>(val, a, lg & 4);
+    halve<NOP / 2, 2>(a, b, lg & 2);
+    halve<NOP / 4, 1>(b, out, lg & 1);
+  }
+}
+
+// Buffers of the cell-kernel epilogue.
+//   MODE 0: L, Lt (FP64, caller's)
+//   MODE 1: Qs = Q* and inc = dt L + dt^2/6 L_t, both in the flux precision R
+//           (the stage-2 kernels read Q* in R; nothing is lost)
+//   MODE 2: Qn (FP64 state, updated in place) += inc + dt^2/3 L_t(Q*)
+template <class R>
+struct StageIO {
+  double* L;
+  double* Lt;
+  R* Qs;
+  R* inc;
+  double* Qn;
+};
+
+template <class R, int ORDER, int NQ, int MODE, class Tin>
+__global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) == 4 ? 2 : 1)
+    k_cell(const Tin* __restrict__ Qin, const R* __restrict__ G, const StageIO<R> io, const GasPar<R> gp,
+           const MeshDev m, const double dt, unsigned* __restrict__ flag) {
+  using LY = CellLayout<ORDER, NQ>;
   using S = CellSmem<R, ORDER, NQ>;
-  constexpr int NM = S::NM, NP = S::NP, NC = S::NC, CB = S::CB, NT = n_tmodes(ORDER);
+  constexpr int NM = LY::NM, NP = LY::NP, NC = S::NC, CB = LY::CB, PG = LY::PG, NT = n_tmodes(ORDER);
+  constexpr int NOUT = LY::NOUT, NOP = LY::NOP, RPL = LY::RPL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R(*coef)[CB] = reinterpret_cast<R(*)[CB]>(smem_raw);
-  R(*Fs)[NP][CB] = reinterpret_cast<R(*)[NP][CB]>(smem_raw + S::coef);
-  R(*dB)[NP][3] = reinterpret_cast<R(*)[NP][3]>(smem_raw + S::coef + S::fs);
-  double* invM = reinterpret_cast<double*>(smem_raw + S::coef + S::fs + S::db);
+  R(*red)[2][NOP] = reinterpret_cast<R(*)[2][NOP]>(smem_raw + S::coef);
+  double* invM = reinterpret_cast<double*>(smem_raw + S::coef + S::red);
   int* tix = reinterpret_cast<int*>(invM + NM);  // [3][NM] tangential index, then [3][NM] parity sign
 
-  const int tid = threadIdx.x, nthr = CB * NP;
-  const int c = tid % CB, p = tid / CB;
+  const int tid = threadIdx.x, nthr = LY::WARPS * 32;
+  const int lane = tid & 31, lg = lane % PG;
+  const int cb = (tid >> 5) * LY::CPW + lane / PG;  // cell of this lane within the CTA
   const int i0 = blockIdx.x * CB, j = blockIdx.y, k = blockIdx.z;
   const int nx = m.nx, ny = m.ny, nz = m.nz;
   const long long nc = m.ncell;
@@ -246,18 +347,6 @@ __global__ void __launch_bounds__(CellTile<NQ>::CB* NQ* NQ* NQ)
   for (int e = tid; e < NC * CB; e += nthr) {
     const int cc = e % CB, comp = e / CB, i = i0 + cc;
     coef[comp][cc] = (i < nx) ? (R)__ldg(Qin + (size_t)comp * nc + row + i) : R(0);
-  }
-  for (int e = tid; e < NM * NP * 3; e += nthr) {
-    const int d = e % 3, pp = (e / 3) % NP, mm = e / (3 * NP);
-    const int pa[3] = {pp / (NQ * NQ), (pp / NQ) % NQ, pp % NQ};
-    R v = R(1);
-#pragma unroll
-    for (int dd = 0; dd < 3; ++dd) {
-      const R x = (R)gauss_x(NQ, pa[dd]);
-      const int n = mode_exp(mm, dd);
-      v *= (dd == d) ? dleg<R>(n, x) : leg<R>(n, x);
-    }
-    dB[mm][pp][d] = v;
   }
   for (int e = tid; e < NM; e += nthr) {
     invM[e] = (double)((2 * mode_exp(e, 0) + 1) * (2 * mode_exp(e, 1) + 1) * (2 * mode_exp(e, 2) + 1)) / m.vol;
@@ -269,22 +358,23 @@ __global__ void __launch_bounds__(CellTile<NQ>::CB* NQ* NQ* NQ)
   }
   __syncthreads();
 
-  // interior flux at point p = (a, b, cz) of cell c
-  {
-    const int i = i0 + c;
-    const bool active = i < nx;
-    const int pa[3] = {p / (NQ * NQ), (p / NQ) % NQ, p % NQ};
-    R L1[3][ORDER + 1], dL1[3][ORDER + 1];
+  // ---- interior flux of Eq. (flux-2) at this lane's Gauss point ----
+  const bool active = (lg < NP) && (i0 + cb < nx);
+  const int pp = active ? lg : 0;
+  const int pa[3] = {pp / (NQ * NQ), (pp / NQ) % NQ, pp % NQ};
+  R L1[3][ORDER + 1], dL1[3][ORDER + 1];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const R x = (R)gauss_x(NQ, pa[d]);
+  for (int d = 0; d < 3; ++d) {
+    const R x = gauss_xr<R>(NQ, pa[d]);
 #pragma unroll
-      for (int n = 0; n <= ORDER; ++n) {
-        L1[d][n] = leg<R>(n, x);
-        dL1[d][n] = dleg<R>(n, x);
-      }
+    for (int n = 0; n <= ORDER; ++n) {
+      L1[d][n] = leg<R>(n, x);
+      dL1[d][n] = dleg<R>(n, x);
     }
-    const R sc[3] = {R(2) / (R)m.h[0], R(2) / (R)m.h[1], R(2) / (R)m.h[2]};
+  }
+  const R sc[3] = {mesh_sc<R>(m, 0), mesh_sc<R>(m, 1), mesh_sc<R>(m, 2)};
+  R Fw[3][5], Ftw[3][5];  // w |K| (2/h_d) F_d, same for F_t
+  {
     R q[5], dq[3][5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -292,7 +382,7 @@ __global__ void __launch_bounds__(CellTile<NQ>::CB* NQ* NQ* NQ)
 #pragma unroll
       for (int mm = 0; mm < NM; ++mm) {
         const int e0 = mode_exp(mm, 0), e1 = mode_exp(mm, 1), e2 = mode_exp(mm, 2);
-        const R cv = coef[v * NM + mm][c];
+        const R cv = coef[v * NM + mm][cb];
         s0 += cv * (L1[0][e0] * L1[1][e1] * L1[2][e2]);
         g0 += cv * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
         g1 += cv * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
@@ -304,36 +394,52 @@ __global__ void __launch_bounds__(CellTile<NQ>::CB* NQ* NQ* NQ)
       dq[2][v] = g2 * sc[2];
     }
     R F[3][5], Ft[3][5];
-    const bool ok = interior_flux(q, dq, gp, F, Ft);
+    bool ok = true;
+    if (active) ok = interior_flux(q, dq, gp, F, Ft);
     if (active && !ok) atomicOr(flag, 1u);
-    const R w = active ? (R)(gauss_w(NQ, pa[0]) * gauss_w(NQ, pa[1]) * gauss_w(NQ, pa[2]) * m.vol) : R(0);
+    const R w = active ? gauss_wr<R>(NQ, pa[0]) * gauss_wr<R>(NQ, pa[1]) * gauss_wr<R>(NQ, pa[2]) * mesh_vol<R>(m) : R(0);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const R wd = w * sc[d];
+    for (int d = 0; d < 3; ++d)
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        Fs[d * 5 + v][p][c] = wd * F[d][v];
-        Fs[15 + d * 5 + v][p][c] = wd * Ft[d][v];
+        Fw[d][v] = active ? w * sc[d] * F[d][v] : R(0);
+        Ftw[d][v] = active ? w * sc[d] * Ft[d][v] : R(0);
       }
+  }
+
+  // ---- volume projection: sum over the group's points of Fw . grad B_n (n >= 1) ----
+#pragma unroll
+  for (int kind = 0; kind < 2; ++kind) {
+    R val[NOP];
+#pragma unroll
+    for (int o = 0; o < NOP; ++o) {
+      R c = R(0);
+      if (o < NOUT) {
+        const int v = o / (NM - 1), n = 1 + o % (NM - 1);
+        const int e0 = mode_exp(n, 0), e1 = mode_exp(n, 1), e2 = mode_exp(n, 2);
+        const R(&Fk)[3][5] = kind == 0 ? Fw : Ftw;
+        if (e0 > 0) c += Fk[0][v] * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
+        if (e1 > 0) c += Fk[1][v] * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
+        if (e2 > 0) c += Fk[2][v] * (L1[0][e0] * L1[1][e1] * dL1[2][e2]);
+      }
+      val[o] = c;
     }
+    R outv[RPL];
+    group_reduce<NOP, PG>(val, outv, lg);
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) red[cb][kind][RPL * lg + r] = outv[r];
   }
   __syncthreads();
 
-  // projection, face assembly, inverse mass matrix, stage epilogue
+  // ---- face assembly, inverse mass matrix, stage epilogue (FP64) ----
   for (int o = tid; o < CB * NC; o += nthr) {
     const int cc = o % CB, rest = o / CB, mm = rest % NM, v = rest / NM;
     const int i = i0 + cc;
     if (i >= nx) continue;
-    R sF = R(0), sT = R(0);
-    for (int pp = 0; pp < NP; ++pp) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const R bb = dB[mm][pp][d];
-        sF += Fs[d * 5 + v][pp][cc] * bb;
-        sT += Fs[15 + d * 5 + v][pp][cc] * bb;
-      }
-    }
     const size_t cell = row + i;
+    const size_t idx = (size_t)(v * NM + mm) * nc + cell;
+    R sF = mm == 0 ? R(0) : red[cc][0][v * (NM - 1) + mm - 1];
+    R sT = mm == 0 ? R(0) : red[cc][1][v * (NM - 1) + mm - 1];
 #pragma unroll
     for (int D = 0; D < 3; ++D) {
       const int t = tix[D * NM + mm];
@@ -350,17 +456,20 @@ __global__ void __launch_bounds__(CellTile<NQ>::CB* NQ* NQ* NQ)
       sF += sg * gF[cell] - gF[up];
       sT += sg * gT[cell] - gT[up];
     }
-    const double Lv = (double)sF * invM[mm], Ltv = (double)sT * invM[mm];
-    const size_t idx = (size_t)(v * NM + mm) * nc + cell;
+    // M^-1 and the stage increments in the flux precision R; the
+    // accumulation into the stored FP64 state is the one FP64 operation.
+    const R iM = (R)invM[mm];
+    const R Lv = sF * iM, Ltv = sT * iM;
     if (MODE == MODE_RESIDUAL) {
-      out0[idx] = Lv;
-      out1[idx] = Ltv;
+      io.L[idx] = (double)Lv;
+      io.Lt[idx] = (double)Ltv;
     } else if (MODE == MODE_STAGE1) {
-      const double qn = Qin[idx];
-      out0[idx] = qn + 0.5 * dt * Lv + (dt * dt / 8.0) * Ltv;
-      out1[idx] = qn + dt * Lv + (dt * dt / 6.0) * Ltv;
+      const R h = (R)dt, h2 = (R)(dt * dt);
+      io.Qs[idx] = coef[v * NM + mm][cc] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
+      io.inc[idx] = h * Lv + (h2 * R(1.0 / 6.0)) * Ltv;
     } else {
-      out0[idx] = acc[idx] + (dt * dt / 3.0) * Ltv;
+      const R h2 = (R)(dt * dt);
+      io.Qn[idx] = io.Qn[idx] + (double)(io.inc[idx] + (h2 * R(1.0 / 3.0)) * Ltv);
     }
   }
 }

@@ -37,6 +37,38 @@ __host__ __device__ constexpr double gauss_w(int nq, int a) {
                                                                           : 0.11846344252809454376);
 }
 
+// Node and weight in the flux precision R, selected in R (no FP64 select or
+// conversion in FP32 kernels when the index is a runtime value).
+template <class R>
+__host__ __device__ __forceinline__ R gauss_xr(int nq, int a) {
+  switch (nq) {
+    case 1: return R(0.0);
+    case 2: return a == 0 ? R(-0.57735026918962576451) : R(0.57735026918962576451);
+    case 3: return a == 0 ? R(-0.77459666924148337704) : a == 1 ? R(0.0) : R(0.77459666924148337704);
+    case 4:
+      return a == 0 ? R(-0.86113631159405257522)
+                    : a == 1 ? R(-0.33998104358485626480) : a == 2 ? R(0.33998104358485626480) : R(0.86113631159405257522);
+    default:
+      return a == 0   ? R(-0.90617984593866399280)
+             : a == 1 ? R(-0.53846931010568309104)
+             : a == 2 ? R(0.0)
+             : a == 3 ? R(0.53846931010568309104)
+                      : R(0.90617984593866399280);
+  }
+}
+template <class R>
+__host__ __device__ __forceinline__ R gauss_wr(int nq, int a) {
+  switch (nq) {
+    case 1: return R(1.0);
+    case 2: return R(0.5);
+    case 3: return a == 1 ? R(0.44444444444444444444) : R(0.27777777777777777778);
+    case 4: return (a == 1 || a == 2) ? R(0.32607257743127307131) : R(0.17392742256872692869);
+    default:
+      return a == 2 ? R(0.28444444444444444444)
+                    : (a == 1 || a == 3) ? R(0.23931433524968323402) : R(0.11846344252809454376);
+  }
+}
+
 template <class R>
 __host__ __device__ constexpr R leg(int n, R x) {
   return n == 0 ? R(1) : n == 1 ? x : n == 2 ? R(1.5) * x * x - R(0.5) : R(2.5) * x * x * x - R(1.5) * x;

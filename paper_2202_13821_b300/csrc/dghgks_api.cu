@@ -29,8 +29,8 @@ struct dghgks_ctx {
   double lo[3], hi[3], h[3], vol = 0;
   int order = 0, nq = 0, nm = 0, nt = 0, precision = 0;
   double gamma = 1.4, K = 2.0, mu = 0, Pr = 1, tau_eps = 0;
-  double* Qs = nullptr;   // Q* (stage-1 output)
-  double* Acc = nullptr;  // Q^n + dt L + dt^2/6 L_t
+  void* Qs = nullptr;   // Q* (stage-1 output), flux precision
+  void* Inc = nullptr;  // dt L + dt^2/6 L_t (stage-1 output), flux precision
   void* G = nullptr;      // face moments [3][10][NT][cells], flux precision
   unsigned* flag = nullptr;
   double* part = nullptr;  // reduction partials [kRedBlocks][5]
@@ -44,6 +44,11 @@ struct dghgks_ctx {
   int prof_n = 0;
   cudaEvent_t* prof_ev = nullptr;  // [2 * kProfMax]
   int* prof_kind = nullptr;        // [kProfMax]
+  // captured step graph
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  double* g_Q = nullptr;
+  double g_dt = 0.0;
   char err[512] = {0};
 };
 
@@ -85,8 +90,13 @@ MeshDev mesh_dev(const dghgks_ctx* c) {
   m.ny = c->n[1];
   m.nz = c->n[2];
   m.ncell = c->ncell;
-  for (int d = 0; d < 3; ++d) m.h[d] = c->h[d];
+  for (int d = 0; d < 3; ++d) {
+    m.h[d] = c->h[d];
+    m.sc_f[d] = (float)(2.0 / c->h[d]);
+    m.area_f[d] = (float)(c->vol / c->h[d]);
+  }
   m.vol = c->vol;
+  m.vol_f = (float)c->vol;
   return m;
 }
 
@@ -109,8 +119,10 @@ struct ProfScope {
 
 struct Ops {
   cudaError_t (*set_attrs)();
-  void (*faces)(dghgks_ctx*, const double*, double, cudaStream_t);
-  void (*cell)(dghgks_ctx*, int, const double*, double*, double*, const double*, double, cudaStream_t);
+  // face pass on a state stored in FP64 (q_in_r = false) or in the flux precision
+  void (*faces)(dghgks_ctx*, const void*, bool, double, cudaStream_t);
+  // cell pass: MODE_RESIDUAL (Q, L, Lt), MODE_STAGE1 (Q^n), MODE_STAGE2 (Q^n updated in place)
+  void (*cell)(dghgks_ctx*, int, double*, double*, double*, double, cudaStream_t);
   void (*ek)(dghgks_ctx*, const double*, cudaStream_t);
   size_t r_size;
 };
@@ -124,17 +136,21 @@ struct Impl {
     cudaError_t e = cudaSuccess;
 #define DG_ATTR(fn, bytes)                                                                         \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes));
-    DG_ATTR((k_face<R, ORDER, NQ, 0>), FS::bytes)
-    DG_ATTR((k_face<R, ORDER, NQ, 1>), FS::bytes)
-    DG_ATTR((k_face<R, ORDER, NQ, 2>), FS::bytes)
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_RESIDUAL>), CS::bytes)
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1>), CS::bytes)
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE2>), CS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 0, double>), FS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 1, double>), FS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 2, double>), FS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 0, R>), FS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 1, R>), FS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 2, R>), FS::bytes)
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_RESIDUAL, double>), CS::bytes)
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, double>), CS::bytes)
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE2, R>), CS::bytes)
 #undef DG_ATTR
     return e;
   }
 
-  static void faces(dghgks_ctx* c, const double* Q, double dt, cudaStream_t s) {
+  template <class Tin>
+  static void faces_t(dghgks_ctx* c, const Tin* Q, double dt, cudaStream_t s) {
     const GasPar<R> g = gas_par<R>(c, dt);
     const MeshDev m = mesh_dev(c);
     dim3 grid((c->n[0] + FB - 1) / FB, c->n[1], c->n[2]);
@@ -142,34 +158,46 @@ struct Impl {
     R* G = static_cast<R*>(c->G);
     {
       ProfScope ps(c, 0, s);
-      k_face<R, ORDER, NQ, 0><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
+      k_face<R, ORDER, NQ, 0, Tin><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
     }
     {
       ProfScope ps(c, 1, s);
-      k_face<R, ORDER, NQ, 1><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
+      k_face<R, ORDER, NQ, 1, Tin><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
     }
     {
       ProfScope ps(c, 2, s);
-      k_face<R, ORDER, NQ, 2><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
+      k_face<R, ORDER, NQ, 2, Tin><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
     }
     c->launches += 3;
   }
 
-  static void cell(dghgks_ctx* c, int mode, const double* Qin, double* o0, double* o1, const double* acc, double dt,
-                   cudaStream_t s) {
+  static void faces(dghgks_ctx* c, const void* Q, bool q_in_r, double dt, cudaStream_t s) {
+    if (q_in_r)
+      faces_t<R>(c, static_cast<const R*>(Q), dt, s);
+    else
+      faces_t<double>(c, static_cast<const double*>(Q), dt, s);
+  }
+
+  static void cell(dghgks_ctx* c, int mode, double* Q, double* L, double* Lt, double dt, cudaStream_t s) {
     const GasPar<R> g = gas_par<R>(c, dt);
     const MeshDev m = mesh_dev(c);
-    constexpr int CB = CellTile<NQ>::CB;
-    dim3 grid((c->n[0] + CB - 1) / CB, c->n[1], c->n[2]);
-    dim3 block(CB * NQ * NQ * NQ);
+    using LY = CellLayout<ORDER, NQ>;
+    dim3 grid((c->n[0] + LY::CB - 1) / LY::CB, c->n[1], c->n[2]);
+    dim3 block(LY::WARPS * 32);
     const R* G = static_cast<const R*>(c->G);
+    StageIO<R> io;
+    io.L = L;
+    io.Lt = Lt;
+    io.Qs = static_cast<R*>(c->Qs);
+    io.inc = static_cast<R*>(c->Inc);
+    io.Qn = Q;
     ProfScope ps(c, 3 + mode, s);
     if (mode == MODE_RESIDUAL)
-      k_cell<R, ORDER, NQ, MODE_RESIDUAL><<<grid, block, CS::bytes, s>>>(Qin, G, o0, o1, acc, g, m, dt, c->flag);
+      k_cell<R, ORDER, NQ, MODE_RESIDUAL, double><<<grid, block, CS::bytes, s>>>(Q, G, io, g, m, dt, c->flag);
     else if (mode == MODE_STAGE1)
-      k_cell<R, ORDER, NQ, MODE_STAGE1><<<grid, block, CS::bytes, s>>>(Qin, G, o0, o1, acc, g, m, dt, c->flag);
+      k_cell<R, ORDER, NQ, MODE_STAGE1, double><<<grid, block, CS::bytes, s>>>(Q, G, io, g, m, dt, c->flag);
     else
-      k_cell<R, ORDER, NQ, MODE_STAGE2><<<grid, block, CS::bytes, s>>>(Qin, G, o0, o1, acc, g, m, dt, c->flag);
+      k_cell<R, ORDER, NQ, MODE_STAGE2, R><<<grid, block, CS::bytes, s>>>(io.Qs, G, io, g, m, dt, c->flag);
     c->launches += 1;
   }
 
@@ -232,6 +260,8 @@ int read_flag(dghgks_ctx* c, cudaStream_t s) {
 
 extern "C" {
 
+static void enqueue_step(dghgks_ctx* c, double* Q, double dt, cudaStream_t s);
+
 int dghgks_gauss_rule(int n, double* x, double* w) {
   if (n < 1 || n > 5 || !x || !w) return DGHGKS_EARG;
   for (int a = 0; a < n; ++a) {
@@ -288,12 +318,12 @@ int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, dou
   c->tau_eps = tau_eps;
   c->ops = ops;
 
-  const size_t state = sizeof(double) * 5 * (size_t)c->nm * c->ncell;
+  const size_t stage = ops->r_size * 5 * (size_t)c->nm * c->ncell;
   const size_t gbytes = ops->r_size * 30 * (size_t)c->nt * c->ncell;
   int rc = DGHGKS_OK;
   if (!rc) rc = cuda_check(c, ops->set_attrs(), "cudaFuncSetAttribute");
-  if (!rc) rc = cuda_check(c, cudaMalloc(&c->Qs, state), "cudaMalloc(Q*)");
-  if (!rc) rc = cuda_check(c, cudaMalloc(&c->Acc, state), "cudaMalloc(Acc)");
+  if (!rc) rc = cuda_check(c, cudaMalloc(&c->Qs, stage), "cudaMalloc(Q*)");
+  if (!rc) rc = cuda_check(c, cudaMalloc(&c->Inc, stage), "cudaMalloc(stage increment)");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->G, gbytes), "cudaMalloc(face moments)");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->flag, sizeof(unsigned)), "cudaMalloc(flag)");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->part, sizeof(double) * 5 * kRedBlocks), "cudaMalloc(partials)");
@@ -311,13 +341,15 @@ int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, dou
 
 void dghgks_destroy(dghgks_ctx* c) {
   if (!c) return;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->prof_ev) {
     for (int e = 0; e < 2 * kProfMax; ++e) cudaEventDestroy(c->prof_ev[e]);
     delete[] c->prof_ev;
     delete[] c->prof_kind;
   }
   cudaFree(c->Qs);
-  cudaFree(c->Acc);
+  cudaFree(c->Inc);
   cudaFree(c->G);
   cudaFree(c->flag);
   cudaFree(c->part);
@@ -346,8 +378,8 @@ int dghgks_residual(dghgks_ctx* c, const double* Q, double dt, double* L, double
   if (!(dt > 0)) return fail(c, DGHGKS_EARG, "dt must be > 0");
   if (L == Q || Lt == Q || L == Lt) return fail(c, DGHGKS_EARG, "L, Lt and Q must be distinct buffers");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  c->ops->faces(c, Q, dt, s);
-  c->ops->cell(c, MODE_RESIDUAL, Q, L, Lt, nullptr, dt, s);
+  c->ops->faces(c, Q, false, dt, s);
+  c->ops->cell(c, MODE_RESIDUAL, const_cast<double*>(Q), L, Lt, dt, s);
   return after_launch(c, "residual launch");
 }
 
@@ -355,14 +387,59 @@ int dghgks_step(dghgks_ctx* c, double* Q, double dt, void* stream) {
   if (!c) return DGHGKS_EARG;
   if (!Q) return fail(c, DGHGKS_EARG, "Q is NULL");
   if (!(dt > 0)) return fail(c, DGHGKS_EARG, "dt must be > 0");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // stage 1 at Q^n
-  c->ops->faces(c, Q, dt, s);
-  c->ops->cell(c, MODE_STAGE1, Q, c->Qs, c->Acc, nullptr, dt, s);
-  // stage 2 at Q* (same dt for the flux fit); only L_t(Q*) enters
-  c->ops->faces(c, c->Qs, dt, s);
-  c->ops->cell(c, MODE_STAGE2, c->Qs, Q, nullptr, c->Acc, dt, s);
+  // stage 1 at Q^n, stage 2 at Q* (same dt for the flux fit; only L_t(Q*) enters)
+  enqueue_step(c, Q, dt, static_cast<cudaStream_t>(stream));
   return after_launch(c, "step launch");
+}
+
+// Enqueue the 8 launches of one S2O4 step on s.
+static void enqueue_step(dghgks_ctx* c, double* Q, double dt, cudaStream_t s) {
+  c->ops->faces(c, Q, false, dt, s);
+  c->ops->cell(c, MODE_STAGE1, Q, nullptr, nullptr, dt, s);  // Q*, inc
+  c->ops->faces(c, c->Qs, true, dt, s);
+  c->ops->cell(c, MODE_STAGE2, Q, nullptr, nullptr, dt, s);  // Q += inc + dt^2/3 L_t(Q*)
+}
+
+int dghgks_steps(dghgks_ctx* c, double* Q, double dt, int nsteps, void* stream) {
+  if (!c) return DGHGKS_EARG;
+  if (!Q || nsteps < 0) return fail(c, DGHGKS_EARG, "bad argument");
+  if (!(dt > 0)) return fail(c, DGHGKS_EARG, "dt must be > 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!c->cap_stream)
+    if (int rc = cuda_check(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream"))
+      return rc;
+  if (!c->gexec || c->g_Q != Q || c->g_dt != dt) {
+    const bool prof = c->prof;
+    const int64_t launches = c->launches;
+    c->prof = false;
+    cudaGraph_t graph = nullptr;
+    if (int rc = cuda_check(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "capture"))
+      return rc;
+    enqueue_step(c, Q, dt, c->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    c->prof = prof;
+    c->launches = launches;
+    if (int rc = cuda_check(c, e, "end capture")) return rc;
+    bool updated = false;
+    if (c->gexec) {
+      cudaGraphExecUpdateResultInfo info;
+      updated = cudaGraphExecUpdate(c->gexec, graph, &info) == cudaSuccess;
+      if (!updated) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+      }
+    }
+    if (!updated) e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (int rc = cuda_check(c, e, "graph instantiate")) return rc;
+    c->g_Q = Q;
+    c->g_dt = dt;
+  }
+  for (int n = 0; n < nsteps; ++n)
+    if (int rc = cuda_check(c, cudaGraphLaunch(c->gexec, s), "graph launch")) return rc;
+  c->launches += 8 * (int64_t)nsteps;
+  return DGHGKS_OK;
 }
 
 int dghgks_totals(dghgks_ctx* c, const double* Q, double* out, void* stream) {

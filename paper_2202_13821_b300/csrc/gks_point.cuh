@@ -37,6 +37,37 @@ using std::erfc;
 using std::exp;
 using std::sqrt;
 
+// Division, reciprocal square root and exponential.  The FP64 path uses the
+// IEEE operations; the FP32 path uses the single-instruction approximations
+// of the special-function unit (about 2 ulp), which is well inside the
+// FP32-mixed error budget and avoids the multi-instruction IEEE sequences.
+template <class R>
+DG_HD R fdiv(R a, R b) {
+  return a / b;
+}
+template <class R>
+DG_HD R frsqrt(R x) {
+  return R(1) / sqrt(x);
+}
+template <class R>
+DG_HD R fexp(R x) {
+  return exp(x);
+}
+#ifdef __CUDA_ARCH__
+template <>
+__device__ __forceinline__ float fdiv<float>(float a, float b) {
+  return __fdividef(a, b);
+}
+template <>
+__device__ __forceinline__ float frsqrt<float>(float x) {
+  return rsqrtf(x);
+}
+template <>
+__device__ __forceinline__ float fexp<float>(float x) {
+  return __expf(x);
+}
+#endif
+
 template <class R>
 struct GasPar {
   R K;         // internal degrees of freedom
@@ -73,8 +104,9 @@ DG_HD void full_line(R* m, R U, R h) {
 // u > 0 (sgn = +1) or u < 0 (sgn = -1) half line
 template <class R>
 DG_HD void half_line(R* m, R U, R lam, R h, int sgn) {
-  const R sl = sqrt(lam);
-  const R e = exp(-lam * U * U) * R(0.28209479177387814347) / sl;  // exp(-lam U^2) / (2 sqrt(pi lam))
+  const R rs = frsqrt(lam);
+  const R sl = lam * rs;  // sqrt(lam)
+  const R e = fexp(-lam * U * U) * (R(0.28209479177387814347) * rs);  // exp(-lam U^2) / (2 sqrt(pi lam))
   if (sgn > 0) {
     m[0] = R(0.5) * erfc(-sl * U);
     m[1] = U * m[0] + e;
@@ -93,13 +125,13 @@ struct Prim {
 // conservative -> (rho, U, V, W, lambda = rho / 2p); false if rho or p is not positive
 template <class R>
 DG_HD bool prim_of(const R q[5], R gm1, Prim<R>& p) {
-  const R ir = R(1) / q[0];
+  const R ir = fdiv(R(1), q[0]);
   p.rho = q[0];
   p.U = q[1] * ir;
   p.V = q[2] * ir;
   p.W = q[3] * ir;
   const R pres = gm1 * (q[4] - R(0.5) * (q[1] * p.U + q[2] * p.V + q[3] * p.W));
-  p.lam = R(0.5) * q[0] / pres;
+  p.lam = fdiv(R(0.5) * q[0], pres);
   return (q[0] > R(0)) && (pres > R(0)) && (p.lam < R(1e30)) && (q[0] < R(1e30));
 }
 
@@ -168,7 +200,7 @@ DG_HD void mom_ud_a_psi(const MomTab<R>& t, const R a[5], R s, R out[5]) {
 
 template <class R>
 DG_HD void full_table(const Prim<R>& p, R K, MomTab<R>& t) {
-  const R h = R(0.5) / p.lam;
+  const R h = fdiv(R(0.5), p.lam);
   full_line(t.u, p.U, h);
   full_line(t.v, p.V, h);
   full_line(t.w, p.W, h);
@@ -182,9 +214,9 @@ DG_HD void full_table(const Prim<R>& p, R K, MomTab<R>& t) {
 // a_0 = b_0 - U.a_{1..3} - a_4 E / 2.
 template <class R>
 DG_HD void slope_solve(const Prim<R>& p, R K, const R b[5], R a[5]) {
-  const R E = p.U * p.U + p.V * p.V + p.W * p.W + (K + R(3)) * R(0.5) / p.lam;
+  const R E = p.U * p.U + p.V * p.V + p.W * p.W + fdiv((K + R(3)) * R(0.5), p.lam);
   const R r1 = b[1] - p.U * b[0], r2 = b[2] - p.V * b[0], r3 = b[3] - p.W * b[0];
-  a[4] = R(4) * p.lam * p.lam / (K + R(3)) * (R(2) * b[4] - E * b[0] - R(2) * (p.U * r1 + p.V * r2 + p.W * r3));
+  a[4] = fdiv(R(4) * p.lam * p.lam, K + R(3)) * (R(2) * b[4] - E * b[0] - R(2) * (p.U * r1 + p.V * r2 + p.W * r3));
   const R tl = R(2) * p.lam;
   a[1] = tl * r1 - p.U * a[4];
   a[2] = tl * r2 - p.V * a[4];
@@ -213,7 +245,7 @@ template <class R>
 DG_HD void fit_weights(R tau, R dt, R inv_dt, R wF[6], R wFt[6]) {
   R Eh = R(0), x = R(0);
   if (tau > R(0)) {
-    Eh = exp(R(-0.5) * dt / tau);
+    Eh = fexp(fdiv(R(-0.5) * dt, tau));
     x = tau * inv_dt;
   }
   const R s = R(1) - Eh;
@@ -251,7 +283,7 @@ DG_HD bool iface_side(const R q[5], const R dq[3][5], const GasPar<R>& g, bool p
                                            SideSums<R>& S) {
   Prim<R> p;
   const bool ok = prim_of(q, g.gm1, p);
-  const R ir = R(1) / p.rho;
+  const R ir = fdiv(R(1), p.rho);
   R a[3][5];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -268,7 +300,7 @@ DG_HD bool iface_side(const R q[5], const R dq[3][5], const GasPar<R>& g, bool p
   R A[5];
   slope_solve(p, g.K, bA, A);
   // half-space table along the normal
-  half_line(t.u, p.U, p.lam, R(0.5) / p.lam, SGN);
+  half_line(t.u, p.U, p.lam, fdiv(R(0.5), p.lam), SGN);
   const R r = p.rho;
   mom_psi<0, 0, 0>(t, r, S.Q0);
 #pragma unroll
@@ -284,23 +316,23 @@ DG_HD bool iface_side(const R q[5], const R dq[3][5], const GasPar<R>& g, bool p
 }
 
 template <class R>
-DG_HD bool iface_flux(const R qL[5], const R dqL[3][5], const R qR[5], const R dqR[3][5],
-                                           const GasPar<R>& g, R F[5], R Ft[5]) {
-  const bool pr_fix = (g.pr_fix != R(0));
-  SideSums<R> S;
+DG_HD void iface_zero(SideSums<R>& S) {
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     S.Q0[k] = S.V4[k] = S.V5[k] = S.V6[k] = S.W5[k] = S.W6[k] = R(0);
 #pragma unroll
     for (int i = 0; i < 3; ++i) S.dQ0[i][k] = R(0);
   }
-  bool ok = iface_side<R, +1>(qL, dqL, g, pr_fix, S);
-  ok = iface_side<R, -1>(qR, dqR, g, pr_fix, S) && ok;
+}
 
-  // equilibrium state g_0 and its slopes
+// Equilibrium state g_0 of the interface, its slopes, tau, the time fit, and
+// the flux (local frame) from the side sums of both sides.
+template <class R>
+DG_HD bool iface_finish(const SideSums<R>& S, const GasPar<R>& g, R F[5], R Ft[5]) {
+  const bool pr_fix = (g.pr_fix != R(0));
   Prim<R> p0;
-  ok = prim_of(S.Q0, g.gm1, p0) && ok;
-  const R ir0 = R(1) / p0.rho;
+  const bool ok = prim_of(S.Q0, g.gm1, p0);
+  const R ir0 = fdiv(R(1), p0.rho);
   R ab[3][5];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -319,7 +351,7 @@ DG_HD bool iface_flux(const R qL[5], const R dqL[3][5], const R qR[5], const R d
   slope_solve(p0, g.K, bA, Ab);
 
   // collision time and fit weights
-  const R tau = g.mu * R(2) * p0.lam / p0.rho + g.tau_add;  // mu / p_0 + tau_eps dt
+  const R tau = fdiv(g.mu * R(2) * p0.lam, p0.rho) + g.tau_add;  // mu / p_0 + tau_eps dt
   R wF[6], wFt[6];
   fit_weights(tau, g.dt, g.inv_dt, wF, wFt);
 
@@ -352,6 +384,17 @@ DG_HD bool iface_flux(const R qL[5], const R dqL[3][5], const R qR[5], const R d
     Ft[4] += g.pr_fix * (wFt[1] * H2 + wFt[2] * H3 + wFt[3] * H4 + wFt[4] * H5 + wFt[5] * H6);
   }
   return ok;
+}
+
+template <class R>
+DG_HD bool iface_flux(const R qL[5], const R dqL[3][5], const R qR[5], const R dqR[3][5], const GasPar<R>& g, R F[5],
+                      R Ft[5]) {
+  const bool pr_fix = (g.pr_fix != R(0));
+  SideSums<R> S;
+  iface_zero(S);
+  bool ok = iface_side<R, +1>(qL, dqL, g, pr_fix, S);
+  ok = iface_side<R, -1>(qR, dqR, g, pr_fix, S) && ok;
+  return iface_finish(S, g, F, Ft) && ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -410,7 +453,7 @@ DG_HD bool interior_flux(const R q[5], const R dq[3][5], const GasPar<R>& g, R F
                                               R Ft[3][5]) {
   Prim<R> p;
   const bool ok = prim_of(q, g.gm1, p);
-  const R ir = R(1) / p.rho;
+  const R ir = fdiv(R(1), p.rho);
   R a[3][5];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -427,7 +470,7 @@ DG_HD bool interior_flux(const R q[5], const R dq[3][5], const GasPar<R>& g, R F
 #pragma unroll
   for (int k = 0; k < 5; ++k) bA[k] = -Wau[k];
   slope_solve(p, g.K, bA, A);
-  const R tau = g.mu * R(2) * p.lam / p.rho + g.tau_add;
+  const R tau = fdiv(g.mu * R(2) * p.lam, p.rho) + g.tau_add;
   interior_dir<0>(t, p, a, A, Wau, tau, g, F[0], Ft[0]);
   interior_dir<1>(t, p, a, A, Wau, tau, g, F[1], Ft[1]);
   interior_dir<2>(t, p, a, A, Wau, tau, g, F[2], Ft[2]);

@@ -1,0 +1,168 @@
+"""Properties of the CUDA path that hold at any size (GPU, through the C ABI).
+
+* optimal order k+1 on the 3D density advection (Sec. 5.1) against its exact
+  solution, on finer grids than the oracle reaches;
+* conservation of mass, momentum and energy to rounding over many steps
+  (FP64 rounding on the FP64 path, FP32 rounding of the per-step increments
+  on the FP32-mixed path);
+* uniform flow preserved; bitwise determinism run to run;
+* graph replay (dghgks_steps) bitwise equal to single steps;
+* FP32-mixed error against the FP64 path on the Taylor-Green vortex, stated
+  and bounded;
+* error paths: non-physical state -> DGHGKS_EPHYS via the device flag (the
+  context stays usable), bad arguments -> DGHGKS_EARG.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def api(torch):
+    from paper_2202_13821_b300 import api, build
+
+    build.build()
+    api.load()
+    return api
+
+
+TGV = dict(lo=(-math.pi,) * 3, hi=(math.pi,) * 3)
+
+
+def advection_error(api, torch, order, n, T=0.1):
+    import oracle
+    from paper_2202_13821_b300 import inputs
+
+    dt = inputs.advection_dt(n, T=T)
+    s = api.Solver((n,) * 3, (0,) * 3, (2,) * 3, order=order, n_q=order + 1, tau_eps=0.01)
+    pb = oracle.Problem(order=order, nq=order + 1, n=(n,) * 3, tau_eps=0.01)
+    Q = torch.from_numpy(oracle.project(pb, oracle.IC_ADVECTION, (0.2, 0.0))).cuda()
+    s.step(Q, dt, round(T / dt))
+    s.status()
+    return oracle.density_errors(pb, Q.cpu().numpy(), oracle.IC_ADVECTION, (0.2, T))
+
+
+@pytest.mark.parametrize("order,sizes,lo_order", [(1, (16, 32), 1.9), (2, (8, 16), 2.85)])
+def test_advection_convergence_order(torch, api, order, sizes, lo_order):
+    e = [advection_error(api, torch, order, n) for n in sizes]
+    orders = np.log2(e[0] / e[1])
+    assert orders[0] > lo_order and orders[1] > lo_order, orders
+
+
+def test_conservation_over_steps(torch, api):
+    from paper_2202_13821_b300 import inputs
+
+    for prec in (0, 1):
+        s = api.Solver((24, 20, 16), **TGV, order=2, mu=1 / 1600, Pr=0.72, n_q=3, precision=prec)
+        Q = inputs.tgv_state((24, 20, 16), 2, perturb=1e-3, device="cuda")
+        t0 = s.totals(Q)
+        s.step(Q, 5e-3, 10)
+        s.status()
+        t1 = s.totals(Q)
+        scale = np.array([1.0, 1.0, 1.0, 1.0, 180.0]) * (2 * math.pi) ** 3
+        # FP64: every face moment enters its two cells with opposite signs and the
+        # sums are FP64.  FP32-mixed: the same antisymmetry, but each cell's stage
+        # increment is rounded to FP32 before the FP64 accumulation, so totals
+        # move by FP32 rounding of the increments (~1e-7 of |dt L| per cell).
+        tol = 1e-13 if prec == 0 else 1e-10
+        assert np.all(np.abs(t1 - t0) <= tol * scale), (prec, (t1 - t0) / scale)
+
+
+def test_uniform_flow_preserved(torch, api):
+    for prec in (0, 1):
+        s = api.Solver((8, 9, 10), (0,) * 3, (1,) * 3, order=2, mu=1e-3, Pr=0.72, precision=prec)
+        Q = torch.zeros(s.shape, dtype=torch.float64, device="cuda")
+        rho, u, p = 1.3, (0.2, -0.4, 0.7), 2.0
+        Q[0, 0], Q[1, 0], Q[2, 0], Q[3, 0] = rho, rho * u[0], rho * u[1], rho * u[2]
+        Q[4, 0] = p / 0.4 + 0.5 * rho * sum(x * x for x in u)
+        L, Lt = s.residual(Q, 1e-2)
+        tol = 1e-12 if prec == 0 else 1e-4
+        assert float(L.abs().max()) < tol and float(Lt.abs().max()) < 10 * tol
+
+
+def test_deterministic_and_graph_replay_bitwise(torch, api):
+    from paper_2202_13821_b300 import inputs
+
+    for prec in (0, 1):
+        s = api.Solver((20, 12, 9), **TGV, order=2, mu=1 / 1600, Pr=0.72, precision=prec)
+        Q0 = inputs.tgv_state((20, 12, 9), 2, perturb=1e-3, device="cuda")
+        A, B, C = Q0.clone(), Q0.clone(), Q0.clone()
+        s.step(A, 4e-3, 3)
+        s.step(B, 4e-3, 3)
+        s.steps(C, 4e-3, 3)
+        s.status()
+        assert torch.equal(A, B) and torch.equal(A, C)
+        # a new dt re-captures the graph
+        D, E = Q0.clone(), Q0.clone()
+        s.steps(D, 2e-3, 2)
+        s.step(E, 2e-3, 2)
+        s.status()
+        assert torch.equal(D, E)
+
+
+def test_fp32_mixed_error_against_fp64(torch, api):
+    """Stated error of the FP32-mixed path on the Taylor-Green vortex (48^3, 10 steps)."""
+    from paper_2202_13821_b300 import inputs
+
+    n = 48
+    dt = inputs.tgv_dt(n, 2)
+    Q0 = inputs.tgv_state(n, 2, device="cuda")
+    res = {}
+    for prec in (0, 1):
+        s = api.Solver((n,) * 3, **TGV, order=2, mu=1 / 1600, Pr=0.72, precision=prec)
+        Q = Q0.clone()
+        ek = [s.kinetic_energy(Q)]
+        for _ in range(10):
+            s.step(Q, dt)
+            ek.append(s.kinetic_energy(Q))
+        s.status()
+        res[prec] = (Q, np.array(ek), s)
+    s64 = res[0][2]
+    l2 = s64.l2_diff(res[1][0], res[0][0], 0)
+    change = s64.l2_diff(res[0][0], Q0, 0)
+    dek = np.abs(res[1][1] - res[0][1]) / res[0][1]
+    decay = abs((res[1][1][-1] - res[1][1][0]) - (res[0][1][-1] - res[0][1][0])) / abs(res[0][1][-1] - res[0][1][0])
+    print(f"FP32-mixed vs FP64: L2(rho) {l2:.3e} (change {change:.3e}), E_k rel {dek.max():.2e}, decay rel {decay:.2e}")
+    assert dek.max() < 1e-6
+    assert decay < 1e-3
+    assert l2 < 0.5 * change
+
+
+def test_nonphysical_state_sets_flag_and_context_survives(torch, api):
+    from paper_2202_13821_b300 import inputs
+
+    s = api.Solver((8, 8, 8), **TGV, order=2, mu=1 / 1600)
+    Q = inputs.tgv_state(8, 2, device="cuda")
+    bad = Q.clone()
+    bad[0, 0, 3, 4, 5] = -1.0  # negative density in one cell
+    L, Lt = s.residual(bad, 1e-3)
+    with pytest.raises(api.DghgksError) as e:
+        s.status()
+    assert e.value.code == -4
+    # the flag was cleared and the context still works
+    L, Lt = s.residual(Q, 1e-3)
+    s.status()
+    assert torch.isfinite(L).all()
+
+
+def test_bad_arguments(torch, api):
+    s = api.Solver((4, 4, 4), (0,) * 3, (1,) * 3, order=1)
+    Q = torch.zeros(s.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(api.DghgksError) as e:
+        api.dghgks_step(s.ctx, Q, -1.0)
+    assert e.value.code == -1
+    with pytest.raises(api.DghgksError) as e:
+        api.dghgks_residual(s.ctx, Q, 1e-3, Q, Q)  # aliasing outputs
+    assert e.value.code == -1
