@@ -50,6 +50,7 @@ extern "C" {
 #define DGHGKS_ECUDA (-3)
 #define DGHGKS_EPHYS (-4)
 #define DGHGKS_ENOMEM (-5)
+#define DGHGKS_ESCRATCH (-6) /* problem too large for dghgks_residual_static's fixed scratch */
 
 #define DGHGKS_FP64 0       /* flux and quadrature arithmetic in FP64 */
 #define DGHGKS_FP32_MIXED 1 /* flux/quadrature in FP32; stage arithmetic and reductions FP64 */
@@ -157,6 +158,32 @@ int dghgks_profile_read(dghgks_ctx* ctx, double* ms, int64_t* launches);
 
 /* Kernel launches made by this context since creation (all entry points). */
 int64_t dghgks_launch_count(const dghgks_ctx* ctx);
+
+/* One residual evaluation (as dghgks_residual) that allocates no memory and
+ * needs no context.  The paper has no counterpart: this is an interface for
+ * callers that cannot call cudaMalloc/cudaFree when they need a residual --
+ * code running inside another framework's memory plan (a caching allocator
+ * that owns the free device memory, a budget fixed at start-up), real-time or
+ * embedded loops that forbid allocation after initialisation, and code that
+ * must not trigger the device-wide synchronisation of cudaFree.
+ * Arguments are those of dghgks_init plus those of dghgks_residual; the caller
+ * passes Q, L, Lt (device, state layout, distinct buffers).
+ * Scratch: the face moments live in one file-scope __device__ array of
+ * DGHGKS_STATIC_SCRATCH_BYTES (16 MiB), which every GPU that loads the library
+ * holds until the process exits; problems needing more
+ * (bytes = 30 * (k+1)(k+2)/2 * cells * (8 for FP64, 4 for FP32-mixed); e.g.
+ * P2 FP64 up to 11650 cells) are rejected with DGHGKS_ESCRATCH before any GPU
+ * work.  The first call on each device (with that device current) looks up
+ * the array's device address and sets kernel attributes; make that first call
+ * before any stream capture.  All calls share the array and a device flag,
+ * which keep the last call's contents (the flag is cleared at each call), so
+ * calls that overlap on the GPU -- concurrent streams, host threads or devices
+ * sharing nothing else -- race: serialise them.  Synchronises `stream`;
+ * returns 0, DGHGKS_EARG, DGHGKS_EUNSUP, DGHGKS_ESCRATCH, DGHGKS_ECUDA, or
+ * DGHGKS_EPHYS if a non-physical state was met (no error text is kept). */
+#define DGHGKS_STATIC_SCRATCH_BYTES (16u << 20)
+int dghgks_residual_static(const dghgks_mesh* mesh, int order, double gamma, double mu, double Pr,
+                           const dghgks_opts* opts, const double* Q, double dt, double* L, double* Lt, void* stream);
 
 /* Gauss-Legendre rule used on the device: nodes x[n] ascending on [-1,1],
  * weights w[n] normalised to sum 1 (n = 1..5).  Host-only, no GPU needed. */

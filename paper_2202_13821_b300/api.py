@@ -20,7 +20,8 @@ _SO = os.path.join(_HERE, "libdghgks.so")
 
 DGHGKS_FP64 = 0
 DGHGKS_FP32_MIXED = 1
-ERRORS = {-1: "bad argument", -2: "unsupported", -3: "CUDA error", -4: "non-physical state", -5: "out of memory"}
+ERRORS = {-1: "bad argument", -2: "unsupported", -3: "CUDA error", -4: "non-physical state", -5: "out of memory",
+          -6: "problem exceeds the fixed scratch of dghgks_residual_static"}
 
 
 class DghgksError(RuntimeError):
@@ -60,6 +61,8 @@ _SIGS = {
     "dghgks_status": (_I, [_VP, _VP]),
     "dghgks_launch_count": (ctypes.c_int64, [_VP]),
     "dghgks_gauss_rule": (_I, [_I, _DP, _DP]),
+    "dghgks_residual_static": (_I, [ctypes.POINTER(Mesh), _I, _D, _D, _D, ctypes.POINTER(Opts), _VP, _D, _VP, _VP,
+                                    _VP]),
     "dghgks_profile": (_I, [_VP, _I]),
     "dghgks_profile_read": (_I, [_VP, _DP, ctypes.POINTER(ctypes.c_int64)]),
 }
@@ -121,6 +124,20 @@ def dghgks_init(n, lo, hi, order: int, gamma: float, mu: float, Pr: float, n_q: 
     if rc != 0:
         raise DghgksError(rc, load().dghgks_last_error(None).decode())
     return ctx
+
+
+def dghgks_residual_static(n, lo, hi, order: int, gamma: float, mu: float, Pr: float, Q, dt: float, L, Lt,
+                           n_q: int = 0, precision: int = DGHGKS_FP64, tau_eps: float = 0.0, stream=None):
+    """Residual without allocation or context (scratch in a fixed device array); see include/dghgks.h."""
+    m = Mesh()
+    m.nx, m.ny, m.nz = (int(v) for v in n)
+    for d in range(3):
+        m.lo[d], m.hi[d], m.periodic[d] = lo[d], hi[d], 1
+    o = Opts(int(n_q), int(precision), float(tau_eps))
+    rc = load().dghgks_residual_static(ctypes.byref(m), int(order), gamma, mu, Pr, ctypes.byref(o), _ptr(Q), dt,
+                                       _ptr(L), _ptr(Lt), _stream(stream))
+    if rc != 0:
+        raise DghgksError(rc, "dghgks_residual_static")
 
 
 def dghgks_destroy(ctx):

@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SO = os.path.join(HERE, "libdghgks.so")
-SOURCES = [os.path.join(HERE, "csrc", "dghgks_api.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "dghgks_api.cu"), os.path.join(HERE, "csrc", "dghgks_static.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc")) if f.endswith((".cu", ".cuh"))] + [
     os.path.join(ROOT, "include", "dghgks.h")]
 
