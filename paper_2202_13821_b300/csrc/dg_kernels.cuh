@@ -84,20 +84,27 @@ __device__ __forceinline__ float mesh_vol<float>(const MeshDev& m) {
 
 constexpr int FB = 32;  // faces per CTA in k_face
 
-// CTAs per SM requested for k_face (the FP32 path trades a few spills for a
-// second resident CTA; the FP64 path is bound by the FP64 pipe)
-#ifndef FACE_MIN_BLOCKS_F32
-#define FACE_MIN_BLOCKS_F32 2
-#endif
-#define FACE_MIN_BLOCKS(R) (sizeof(R) == 4 ? FACE_MIN_BLOCKS_F32 : 1)
+// Register cap of k_face.  The register file of an SM is split between its
+// four sub-partitions (16384 registers each) and a CTA's warps are spread
+// over them, so the cap for C resident CTAs of W warps is
+// 16384 / (ceil(C W / 4) x 32), rounded down to a multiple of 8.
+// FP32: 2 CTAs of 9 warps (n_q = 3; 96 registers, a few spills) or 4 CTAs of
+// 4 warps (n_q = 2; 128 registers).  FP64 (bound by the FP64 pipe): 1 CTA.
+template <class R, int NQ>
+constexpr int face_max_regs() {
+  constexpr int warps = (FB * NQ * NQ + 31) / 32;
+  constexpr int ctas = sizeof(R) == 4 ? (NQ >= 3 ? 2 : 4) : 1;
+  constexpr int per_part = (warps * ctas + 3) / 4;
+  constexpr int cap = 16384 / (per_part * 32) / 8 * 8;
+  return cap > 255 ? 255 : cap;
+}
 
 template <class R, int ORDER, int NQ>
 struct FaceSmem {
   static constexpr int NM = n_modes(ORDER), NT = n_tmodes(ORDER), NP = NQ * NQ, NC = 5 * NM;
   static constexpr size_t coef = sizeof(R) * NC * FB;  // one side
   static constexpr size_t fs = sizeof(R) * 10 * NP * FB;
-  static constexpr size_t phi = sizeof(R) * NT * NP;
-  static constexpr size_t bytes = 2 * coef + fs + phi;
+  static constexpr size_t bytes = 2 * coef + fs;
 };
 
 __device__ __forceinline__ int wrapm(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
@@ -106,7 +113,7 @@ __device__ __forceinline__ int wrapm(int i, int n) { return i < 0 ? i + n : (i >
 // Face kernel
 // ---------------------------------------------------------------------------
 template <class R, int ORDER, int NQ, int D, class Tin>
-__global__ void __launch_bounds__(FB* NQ* NQ, FACE_MIN_BLOCKS(R))
+__global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>()))
     k_face(const Tin* __restrict__ Q, R* __restrict__ G, const GasPar<R> gp, const MeshDev m,
            unsigned* __restrict__ flag) {
   using S = FaceSmem<R, ORDER, NQ>;
@@ -116,7 +123,6 @@ __global__ void __launch_bounds__(FB* NQ* NQ, FACE_MIN_BLOCKS(R))
   R(*cL)[FB] = reinterpret_cast<R(*)[FB]>(smem_raw);
   R(*cR)[FB] = reinterpret_cast<R(*)[FB]>(smem_raw + S::coef);
   R(*Fs)[NP][FB] = reinterpret_cast<R(*)[NP][FB]>(smem_raw + 2 * S::coef);
-  R(*phi)[NP] = reinterpret_cast<R(*)[NP]>(smem_raw + 2 * S::coef + S::fs);
 
   const int tid = threadIdx.x;
   const int f = tid % FB, p = tid / FB;
@@ -142,10 +148,6 @@ __global__ void __launch_bounds__(FB* NQ* NQ, FACE_MIN_BLOCKS(R))
       cL[c][ff] = val;
     else
       cR[c][ff] = val;
-  }
-  for (int e = tid; e < NT * NP; e += FB * NP) {
-    const int t = e / NP, pp = e % NP;
-    phi[t][pp] = leg<R>(tmode_p(t), gauss_xr<R>(NQ, pp / NQ)) * leg<R>(tmode_q(t), gauss_xr<R>(NQ, pp % NQ));
   }
   __syncthreads();
 
@@ -232,15 +234,23 @@ __global__ void __launch_bounds__(FB* NQ* NQ, FACE_MIN_BLOCKS(R))
   Fs[9][p][f] = w * Ftl[4];
   __syncthreads();
 
-  // tangential projection: G[D][c][t][face] = sum_p Fs[c][p] phi_t(p)
+  // tangential projection G[D][c][t][face] = sum_p Fs[c][p] phi_t(p): the
+  // thread with point index p takes components c = p, p + NP, ...; the
+  // Legendre products phi_t(p) are compile-time constants.
   if (active) {
     const size_t face = ((size_t)k * ny + j) * nx + i;
-    for (int o = p; o < 10 * NT; o += NP) {
-      const int c = o / NT, t = o % NT;
-      R s = R(0);
+    for (int c = p; c < 10; c += NP) {
+      R fv[NP];
 #pragma unroll
-      for (int pp = 0; pp < NP; ++pp) s += Fs[c][pp][f] * phi[t][pp];
-      G[((size_t)(D * 10 + c) * NT + t) * nc + face] = s;
+      for (int pp = 0; pp < NP; ++pp) fv[pp] = Fs[c][pp][f];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        R s = R(0);
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp)
+          s += fv[pp] * (leg<R>(tmode_p(t), gauss_xr<R>(NQ, pp / NQ)) * leg<R>(tmode_q(t), gauss_xr<R>(NQ, pp % NQ)));
+        G[((size_t)(D * 10 + c) * NT + t) * nc + face] = s;
+      }
     }
   }
 }
