@@ -145,6 +145,35 @@ int dghgks_l2_diff(dghgks_ctx* ctx, const double* A, const double* B, int var, d
  * cleared), DGHGKS_ECUDA on a CUDA error, else 0. */
 int dghgks_status(dghgks_ctx* ctx, void* stream);
 
+/* ---- adjoint (reverse mode, FP64 contexts only; the paper has none) ----
+ * The vector-Jacobian products below are exact to rounding: the point-flux
+ * Jacobians come from forward-mode dual numbers through the same flux code,
+ * the projection and trace operators are transposed exactly.  They allocate
+ * adjoint scratch on first use (face cotangents 3 x 2 x 5 N_m doubles per
+ * cell, a state-sized buffer, per-CTA partials).  FP32-mixed contexts return
+ * DGHGKS_EUNSUP. */
+
+/* (lamQ, dmu) = (dL/dQ, dL/dmu)^T lamL + (dL_t/dQ, dL_t/dmu)^T lamLt at Q for
+ * the residual of dghgks_residual with the same dt.  lamQ (device, state
+ * layout) is overwritten; the viscosity cotangent is ADDED to the device
+ * scalar *dmu.  Asynchronous. */
+int dghgks_residual_vjp(dghgks_ctx* ctx, const double* Q, double dt, const double* lamL, const double* lamLt,
+                        double* lamQ, double* dmu, void* stream);
+
+/* Adjoint of one S2O4 step (Eq. two-stage) from the checkpoint Q^n:
+ * lam_n = (dQ^{n+1}/dQ^n)^T lam_next, and (dQ^{n+1}/dmu)^T lam_next is ADDED to
+ * the device scalar *dJ_dmu.  Q* is recomputed from Q^n (one forward stage);
+ * then the stage-2 VJP at Q* with cotangent (0, dt^2/3 lam) gives lam*, and
+ * the stage-1 VJP at Q^n with (dt lam + dt/2 lam*, dt^2/6 lam + dt^2/8 lam*)
+ * gives the rest: lam_n = lam + lam* + VJP.  lam_n may alias lam_next.
+ * Asynchronous. */
+int dghgks_adjoint_step(dghgks_ctx* ctx, const double* Qn, const double* lam_next, double dt, double* lam_n,
+                        double* dJ_dmu, void* stream);
+
+/* Gradient of dghgks_kinetic_energy with respect to Q (device, state layout,
+ * overwritten).  Works on any context (FP64 arithmetic).  Asynchronous. */
+int dghgks_kinetic_energy_vjp(dghgks_ctx* ctx, const double* Q, double rho0, double* dEk_dQ, void* stream);
+
 /* Per-kernel timing with CUDA events recorded on the launching stream around
  * every launch of this context.  enable = 1 starts (and clears) the record,
  * 0 stops it.  Kernel kinds: 0..2 face flux for normals x, y, z; 3 cell

@@ -63,6 +63,9 @@ _SIGS = {
     "dghgks_gauss_rule": (_I, [_I, _DP, _DP]),
     "dghgks_residual_static": (_I, [ctypes.POINTER(Mesh), _I, _D, _D, _D, ctypes.POINTER(Opts), _VP, _D, _VP, _VP,
                                     _VP]),
+    "dghgks_residual_vjp": (_I, [_VP, _VP, _D, _VP, _VP, _VP, _VP, _VP]),
+    "dghgks_adjoint_step": (_I, [_VP, _VP, _VP, _D, _VP, _VP, _VP]),
+    "dghgks_kinetic_energy_vjp": (_I, [_VP, _VP, _D, _VP, _VP]),
     "dghgks_profile": (_I, [_VP, _I]),
     "dghgks_profile_read": (_I, [_VP, _DP, ctypes.POINTER(ctypes.c_int64)]),
 }
@@ -198,6 +201,21 @@ def dghgks_gauss_rule(n: int):
     if rc:
         raise DghgksError(rc, "gauss rule")
     return x, w
+
+
+def dghgks_residual_vjp(ctx, Q, dt: float, lamL, lamLt, lamQ, dmu, stream=None):
+    """lamQ <- (dL/dQ)^T lamL + (dLt/dQ)^T lamLt; dmu (1-element CUDA tensor) += viscosity part."""
+    _check(ctx, load().dghgks_residual_vjp(ctx, _ptr(Q), dt, _ptr(lamL), _ptr(lamLt), _ptr(lamQ), _ptr(dmu),
+                                           _stream(stream)))
+
+
+def dghgks_adjoint_step(ctx, Qn, lam_next, dt: float, lam_n, dJ_dmu, stream=None):
+    _check(ctx, load().dghgks_adjoint_step(ctx, _ptr(Qn), _ptr(lam_next), dt, _ptr(lam_n), _ptr(dJ_dmu),
+                                           _stream(stream)))
+
+
+def dghgks_kinetic_energy_vjp(ctx, Q, rho0: float, out, stream=None):
+    _check(ctx, load().dghgks_kinetic_energy_vjp(ctx, _ptr(Q), rho0, _ptr(out), _stream(stream)))
 
 
 def dghgks_profile(ctx, enable: bool):

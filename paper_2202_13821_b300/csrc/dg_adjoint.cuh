@@ -1,0 +1,520 @@
+// Reverse-mode (adjoint) kernels of the DG-HGKS residual, FP64.
+//
+// The residual of Sec. 3 (Eq. operator) is a linear projection of point
+// fluxes, which are nonlinear functions of the traces, which are linear in
+// the modal coefficients:
+//   Q --trace--> (q, grad q)(x_m) --flux (Eq. flux / flux-2)--> F(x_m)
+//     --projection (Eqs. surface, volume)--> R --M^-1--> L.
+// Given cotangents of (L, L_t) the vector-Jacobian product runs backwards:
+//   mu = M^-1 lambda (diagonal); the projection transposed gives the
+//   cotangent of F and F_t at every Gauss point; the point-flux Jacobian
+//   transposed gives the cotangents of the traces and of the viscosity; the
+//   trace transposed gives the cotangent of Q.
+// The point-flux Jacobian-transpose products use forward-mode dual numbers
+// through the same templated flux code as the forward kernels: one dual pass
+// per input direction (41 at a face point: both sides' traces and
+// gradients and mu; 21 at a cell point), each dotted with the point's flux
+// cotangent.  Exact to rounding; every sum is taken in a fixed order.
+#pragma once
+#include <cmath>
+
+#include "dg_kernels.cuh"
+
+namespace dghgks {
+
+// ---- forward-mode dual number (value, one directional derivative) ----
+struct DualD {
+  double v, d;
+  DG_HD DualD() : v(0.0), d(0.0) {}
+  DG_HD DualD(double x) : v(x), d(0.0) {}
+  DG_HD DualD(double x, double dx) : v(x), d(dx) {}
+};
+DG_HD DualD operator+(DualD a, DualD b) { return DualD(a.v + b.v, a.d + b.d); }
+DG_HD DualD operator-(DualD a, DualD b) { return DualD(a.v - b.v, a.d - b.d); }
+DG_HD DualD operator-(DualD a) { return DualD(-a.v, -a.d); }
+DG_HD DualD operator*(DualD a, DualD b) { return DualD(a.v * b.v, a.d * b.v + a.v * b.d); }
+DG_HD DualD operator/(DualD a, DualD b) {
+  const double q = a.v / b.v;
+  return DualD(q, (a.d - q * b.d) / b.v);
+}
+DG_HD DualD& operator+=(DualD& a, DualD b) {
+  a = a + b;
+  return a;
+}
+DG_HD bool operator>(DualD a, DualD b) { return a.v > b.v; }
+DG_HD bool operator<(DualD a, DualD b) { return a.v < b.v; }
+DG_HD bool operator!=(DualD a, DualD b) { return a.v != b.v; }
+DG_HD DualD exp(DualD a) {
+  const double e = ::exp(a.v);
+  return DualD(e, e * a.d);
+}
+DG_HD DualD sqrt(DualD a) {
+  const double r = ::sqrt(a.v);
+  return DualD(r, a.d / (2.0 * r));
+}
+DG_HD DualD erfc(DualD a) {
+  // d/dx erfc(x) = -2/sqrt(pi) exp(-x^2)
+  return DualD(::erfc(a.v), -1.12837916709551257390 * ::exp(-a.v * a.v) * a.d);
+}
+
+// Adjoint scratch of one stage: face cotangents H[D][side][comp][face]
+// (side 0 = left cell of the face, 1 = right cell; comp = v * NM + n).
+struct AdjIO {
+  const double* lamA;  // first cotangent input (state layout)
+  const double* lamB;  // second cotangent input (may be NULL)
+  double cLA, cLB;     // lambda_L  = cLA lamA + cLB lamB
+  double cTA, cTB;     // lambda_Lt = cTA lamA + cTB lamB
+  double* H;           // face cotangents
+  double* out;         // cotangent of Q (state layout)
+  const double* addA;  // out = addA + addB + J^T lambda (either may be NULL)
+  const double* addB;
+  double* mu_part;     // per-CTA partial sums of the viscosity cotangent
+};
+
+template <int ORDER, int NQ>
+struct FaceAdjSmem {
+  static constexpr int NM = n_modes(ORDER), NP = NQ * NQ, NC = 5 * NM;
+  static constexpr size_t coef = sizeof(double) * NC * FB;  // one side, one array
+  static constexpr size_t g = sizeof(double) * 40 * NP * FB;
+  static constexpr size_t red = sizeof(double) * FB * NP;
+  static constexpr size_t bytes = 2 * coef + 4 * coef + g + red + sizeof(double) * NM;
+};
+
+// cotangent scale of mode n: lambda_R = M^-1 lambda_L with M^-1 = prod(2 n_d + 1) / |K|
+DG_HD double inv_mass(int mm, double vol) {
+  return (double)((2 * mode_exp(mm, 0) + 1) * (2 * mode_exp(mm, 1) + 1) * (2 * mode_exp(mm, 2) + 1)) / vol;
+}
+
+// ---------------------------------------------------------------------------
+// Face VJP: H[D][side][comp][face] = sum over the face's Gauss points of the
+// trace transpose of the traces' cotangents; mu_part[block] = viscosity part.
+// ---------------------------------------------------------------------------
+template <int ORDER, int NQ, int D>
+__global__ void __launch_bounds__(FB* NQ* NQ)
+    k_face_vjp(const double* __restrict__ Q, const GasPar<double> gp, const MeshDev m, const AdjIO io,
+               const size_t mu_offset) {
+  using S = FaceAdjSmem<ORDER, NQ>;
+  constexpr int NM = S::NM, NP = S::NP, NC = S::NC;
+  constexpr int T1 = tan1(D), T2 = tan2(D);
+  constexpr int A0 = D, A1 = (D + 1) % 3, A2 = (D + 2) % 3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double(*cq)[NC][FB] = reinterpret_cast<double(*)[NC][FB]>(smem_raw);                  // [side]
+  double(*cmu)[NC][FB] = reinterpret_cast<double(*)[NC][FB]>(smem_raw + 2 * S::coef);   // [side*2 + kind]
+  double(*gs)[NP][FB] = reinterpret_cast<double(*)[NP][FB]>(smem_raw + 6 * S::coef);   // [input][point]
+  double(*red)[FB] = reinterpret_cast<double(*)[FB]>(smem_raw + 6 * S::coef + S::g);  // [point]
+
+  const int tid = threadIdx.x, nthr = FB * NP;
+  const int f = tid % FB, p = tid / FB;
+  const int i0 = blockIdx.x * FB, j = blockIdx.y, k = blockIdx.z;
+  const int nx = m.nx, ny = m.ny, nz = m.nz;
+  const long long nc = m.ncell;
+
+  // stage Q and the mass-scaled cotangents of both cells of each face
+  for (int e = tid; e < 2 * NC * FB; e += nthr) {
+    const int ff = e % FB, rest = e / FB, c = rest % NC, side = rest / NC;
+    const int i = i0 + ff;
+    double q = 0, mR = 0, mT = 0;
+    if (i < nx) {
+      int ci = i, cj = j, ck = k;
+      if (side == 0) {
+        if (D == 0) ci = wrapm(i - 1, nx);
+        if (D == 1) cj = wrapm(j - 1, ny);
+        if (D == 2) ck = wrapm(k - 1, nz);
+      }
+      const size_t idx = (size_t)c * nc + ((size_t)ck * ny + cj) * nx + ci;
+      const double iM = inv_mass(c % NM, m.vol);
+      const double a = io.lamA[idx], b = io.lamB ? io.lamB[idx] : 0.0;
+      q = Q[idx];
+      mR = iM * (io.cLA * a + io.cLB * b);
+      mT = iM * (io.cTA * a + io.cTB * b);
+    }
+    cq[side][c][ff] = q;
+    cmu[side * 2][c][ff] = mR;
+    cmu[side * 2 + 1][c][ff] = mT;
+  }
+  __syncthreads();
+
+  const int i = i0 + f;
+  const bool active = i < nx;
+  const int a = p / NQ, b = p % NQ;
+  const double xa = gauss_x(NQ, a), xb = gauss_x(NQ, b);
+  double La[ORDER + 1], dLa[ORDER + 1], Lb[ORDER + 1], dLb[ORDER + 1];
+#pragma unroll
+  for (int n = 0; n <= ORDER; ++n) {
+    La[n] = leg<double>(n, xa);
+    dLa[n] = dleg<double>(n, xa);
+    Lb[n] = leg<double>(n, xb);
+    dLb[n] = dleg<double>(n, xb);
+  }
+  const double sD = 2.0 / m.h[D], s1 = 2.0 / m.h[T1], s2 = 2.0 / m.h[T2];
+  const double w = active ? gauss_w(NQ, a) * gauss_w(NQ, b) * (m.vol / m.h[D]) : 0.0;
+
+  // traces (global axes) and the flux cotangents of the point
+  double q[2][5], dq[2][3][5], lF[5], lT[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    lF[v] = 0.0;
+    lT[v] = 0.0;
+  }
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    // the face adds -w F B^L to the left cell and +w F B^R to the right cell
+    const double sg = side == 0 ? -w : w;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double s0 = 0, gD = 0, g1 = 0, g2 = 0;
+#pragma unroll
+      for (int mm = 0; mm < NM; ++mm) {
+        const int nD = mode_exp(mm, D), n1 = mode_exp(mm, T1), n2 = mode_exp(mm, T2);
+        const double pn = (side == 0 || (nD % 2 == 0)) ? 1.0 : -1.0;
+        const double dpn = (double)(nD * (nD + 1) / 2) * ((side == 0 || (nD % 2 == 1)) ? 1.0 : -1.0);
+        const double c = cq[side][v * NM + mm][f];
+        const double B = pn * La[n1] * Lb[n2];
+        s0 += c * B;
+        gD += c * (dpn * La[n1] * Lb[n2]);
+        g1 += c * (pn * dLa[n1] * Lb[n2]);
+        g2 += c * (pn * La[n1] * dLb[n2]);
+        lF[v] += sg * B * cmu[side * 2][v * NM + mm][f];
+        lT[v] += sg * B * cmu[side * 2 + 1][v * NM + mm][f];
+      }
+      q[side][v] = s0;
+      dq[side][D][v] = gD * sD;
+      dq[side][T1][v] = g1 * s1;
+      dq[side][T2][v] = g2 * s2;
+    }
+  }
+
+  // 41 directions: traces of both sides (q: 5, dq: 15 each) and mu
+  double gmu = 0.0;
+  GasPar<DualD> gd;
+  gd.K = DualD(gp.K);
+  gd.gm1 = DualD(gp.gm1);
+  gd.tau_add = DualD(gp.tau_add);
+  gd.pr_fix = DualD(gp.pr_fix);
+  gd.dt = DualD(gp.dt);
+  gd.inv_dt = DualD(gp.inv_dt);
+  for (int dir = 0; dir < 41; ++dir) {
+    gd.mu = DualD(gp.mu, dir == 40 ? 1.0 : 0.0);
+    const bool pr_fix = (gp.pr_fix != 0.0);
+    SideSums<DualD> sums;
+    iface_zero(sums);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      DualD ql[5], dql[3][5], qg[5], dqg[3][5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        qg[v] = DualD(q[side][v], dir == side * 20 + v ? 1.0 : 0.0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) dqg[d][v] = DualD(dq[side][d][v], dir == side * 20 + 5 + d * 5 + v ? 1.0 : 0.0);
+      }
+      const int ax[3] = {A0, A1, A2};
+      ql[0] = qg[0];
+      ql[1] = qg[1 + A0];
+      ql[2] = qg[1 + A1];
+      ql[3] = qg[1 + A2];
+      ql[4] = qg[4];
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii) {
+        dql[ii][0] = dqg[ax[ii]][0];
+        dql[ii][1] = dqg[ax[ii]][1 + A0];
+        dql[ii][2] = dqg[ax[ii]][1 + A1];
+        dql[ii][3] = dqg[ax[ii]][1 + A2];
+        dql[ii][4] = dqg[ax[ii]][4];
+      }
+      if (side == 0)
+        iface_side<DualD, +1>(ql, dql, gd, pr_fix, sums);
+      else
+        iface_side<DualD, -1>(ql, dql, gd, pr_fix, sums);
+    }
+    DualD Fl[5], Ftl[5];
+    iface_finish(sums, gd, Fl, Ftl);
+    // back to global components and dot with the cotangents
+    double gi = lF[0] * Fl[0].d + lF[4] * Fl[4].d + lT[0] * Ftl[0].d + lT[4] * Ftl[4].d;
+    gi += lF[1 + A0] * Fl[1].d + lF[1 + A1] * Fl[2].d + lF[1 + A2] * Fl[3].d;
+    gi += lT[1 + A0] * Ftl[1].d + lT[1 + A1] * Ftl[2].d + lT[1 + A2] * Ftl[3].d;
+    if (!active) gi = 0.0;
+    if (dir < 40)
+      gs[dir][p][f] = gi;
+    else
+      gmu = gi;
+  }
+  red[p][f] = gmu;
+  __syncthreads();
+
+  // trace transpose, summed over the face's points in a fixed order:
+  // H[side][v][n] = sum_p B_n(p) g_q[v] + sum_d (2/h_d) dB_n/dr_d(p) g_dq[d][v]
+  if (active) {
+    const size_t face = ((size_t)k * ny + j) * nx + i;
+    for (int o = p; o < 2 * NC; o += NP) {
+      const int side = o / NC, comp = o % NC, v = comp / NM, mm = comp % NM;
+      const int nD = mode_exp(mm, D), n1 = mode_exp(mm, T1), n2 = mode_exp(mm, T2);
+      const double pn = (side == 0 || (nD % 2 == 0)) ? 1.0 : -1.0;
+      const double dpn = (double)(nD * (nD + 1) / 2) * ((side == 0 || (nD % 2 == 1)) ? 1.0 : -1.0);
+      double acc = 0.0;
+      for (int pp = 0; pp < NP; ++pp) {
+        const double xa2 = gauss_x(NQ, pp / NQ), xb2 = gauss_x(NQ, pp % NQ);
+        const double l1 = leg<double>(n1, xa2), l2 = leg<double>(n2, xb2);
+        const int base = side * 20;
+        acc += pn * l1 * l2 * gs[base + v][pp][f];
+        acc += sD * dpn * l1 * l2 * gs[base + 5 + D * 5 + v][pp][f];
+        acc += s1 * pn * dleg<double>(n1, xa2) * l2 * gs[base + 5 + T1 * 5 + v][pp][f];
+        acc += s2 * pn * l1 * dleg<double>(n2, xb2) * gs[base + 5 + T2 * 5 + v][pp][f];
+      }
+      io.H[(((size_t)D * 2 + side) * NC + comp) * nc + face] = acc;
+    }
+  }
+  // viscosity cotangent: per-CTA partial in a fixed order
+  if (tid == 0) {
+    double s = 0.0;
+    for (int pp = 0; pp < NP; ++pp)
+      for (int ff = 0; ff < FB; ++ff) s += red[pp][ff];
+    const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    io.mu_part[mu_offset + blk] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cell VJP: out = addA + addB + (volume part + the six faces' H) of the cell.
+// ---------------------------------------------------------------------------
+template <int ORDER, int NQ>
+struct CellAdjSmem {
+  using LY = CellLayout<ORDER, NQ>;
+  static constexpr int NM = LY::NM, NC = 5 * NM, CB = LY::CB;
+  static constexpr int NOP2 = (NC + LY::PG - 1) / LY::PG * LY::PG;
+  static constexpr size_t coef = sizeof(double) * NC * CB;
+  static constexpr size_t red = sizeof(double) * CB * NOP2;
+  static constexpr size_t bytes = 3 * coef + red + sizeof(double) * LY::WARPS * 32;
+};
+
+template <int ORDER, int NQ>
+__global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
+    k_cell_vjp(const double* __restrict__ Q, const GasPar<double> gp, const MeshDev m, const AdjIO io,
+               const size_t mu_offset) {
+  using LY = CellLayout<ORDER, NQ>;
+  using S = CellAdjSmem<ORDER, NQ>;
+  constexpr int NM = LY::NM, NP = LY::NP, NC = S::NC, CB = LY::CB, PG = LY::PG, NOP2 = S::NOP2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double(*cq)[CB] = reinterpret_cast<double(*)[CB]>(smem_raw);
+  double(*cmuR)[CB] = reinterpret_cast<double(*)[CB]>(smem_raw + S::coef);
+  double(*cmuT)[CB] = reinterpret_cast<double(*)[CB]>(smem_raw + 2 * S::coef);
+  double(*red)[NOP2] = reinterpret_cast<double(*)[NOP2]>(smem_raw + 3 * S::coef);
+  double* mured = reinterpret_cast<double*>(smem_raw + 3 * S::coef + S::red);
+
+  const int tid = threadIdx.x, nthr = LY::WARPS * 32;
+  const int lane = tid & 31, lg = lane % PG;
+  const int cb = (tid >> 5) * LY::CPW + lane / PG;
+  const int i0 = blockIdx.x * CB, j = blockIdx.y, k = blockIdx.z;
+  const int nx = m.nx, ny = m.ny, nz = m.nz;
+  const long long nc = m.ncell;
+  const size_t row = ((size_t)k * ny + j) * nx;
+
+  for (int e = tid; e < NC * CB; e += nthr) {
+    const int cc = e % CB, comp = e / CB, i = i0 + cc;
+    double q = 0, mR = 0, mT = 0;
+    if (i < nx) {
+      const size_t idx = (size_t)comp * nc + row + i;
+      const double iM = inv_mass(comp % NM, m.vol);
+      const double a = io.lamA[idx], b = io.lamB ? io.lamB[idx] : 0.0;
+      q = Q[idx];
+      mR = iM * (io.cLA * a + io.cLB * b);
+      mT = iM * (io.cTA * a + io.cTB * b);
+    }
+    cq[comp][cc] = q;
+    cmuR[comp][cc] = mR;
+    cmuT[comp][cc] = mT;
+  }
+  __syncthreads();
+
+  const bool active = (lg < NP) && (i0 + cb < nx);
+  const int pp = active ? lg : 0;
+  const int pa[3] = {pp / (NQ * NQ), (pp / NQ) % NQ, pp % NQ};
+  double L1[3][ORDER + 1], dL1[3][ORDER + 1];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double x = gauss_x(NQ, pa[d]);
+#pragma unroll
+    for (int n = 0; n <= ORDER; ++n) {
+      L1[d][n] = leg<double>(n, x);
+      dL1[d][n] = dleg<double>(n, x);
+    }
+  }
+  const double sc[3] = {2.0 / m.h[0], 2.0 / m.h[1], 2.0 / m.h[2]};
+  const double w = active ? gauss_w(NQ, pa[0]) * gauss_w(NQ, pa[1]) * gauss_w(NQ, pa[2]) * m.vol : 0.0;
+
+  // traces and flux cotangents: lambda_F_d[v] = w (2/h_d) sum_n dB_n/dr_d mu_R[v][n]
+  double q[5], dq[3][5], lF[3][5], lT[3][5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    double s0 = 0, g[3] = {0, 0, 0}, f3[3] = {0, 0, 0}, t3[3] = {0, 0, 0};
+#pragma unroll
+    for (int mm = 0; mm < NM; ++mm) {
+      const int e0 = mode_exp(mm, 0), e1 = mode_exp(mm, 1), e2 = mode_exp(mm, 2);
+      const double c = cq[v * NM + mm][cb];
+      const double dB[3] = {dL1[0][e0] * L1[1][e1] * L1[2][e2], L1[0][e0] * dL1[1][e1] * L1[2][e2],
+                            L1[0][e0] * L1[1][e1] * dL1[2][e2]};
+      s0 += c * (L1[0][e0] * L1[1][e1] * L1[2][e2]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        g[d] += c * dB[d];
+        f3[d] += dB[d] * cmuR[v * NM + mm][cb];
+        t3[d] += dB[d] * cmuT[v * NM + mm][cb];
+      }
+    }
+    q[v] = s0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      dq[d][v] = g[d] * sc[d];
+      lF[d][v] = w * sc[d] * f3[d];
+      lT[d][v] = w * sc[d] * t3[d];
+    }
+  }
+
+  // 21 directions: q (5), dq (15), mu
+  double gq[5] = {0, 0, 0, 0, 0}, gdq[3][5] = {{0}}, gmu = 0.0;
+  GasPar<DualD> gd;
+  gd.K = DualD(gp.K);
+  gd.gm1 = DualD(gp.gm1);
+  gd.tau_add = DualD(gp.tau_add);
+  gd.pr_fix = DualD(gp.pr_fix);
+  gd.dt = DualD(gp.dt);
+  gd.inv_dt = DualD(gp.inv_dt);
+  if (active) {
+    for (int dir = 0; dir < 21; ++dir) {
+      gd.mu = DualD(gp.mu, dir == 20 ? 1.0 : 0.0);
+      DualD qd[5], dqd[3][5], F[3][5], Ft[3][5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        qd[v] = DualD(q[v], dir == v ? 1.0 : 0.0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) dqd[d][v] = DualD(dq[d][v], dir == 5 + d * 5 + v ? 1.0 : 0.0);
+      }
+      interior_flux(qd, dqd, gd, F, Ft);
+      double gi = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) gi += lF[d][v] * F[d][v].d + lT[d][v] * Ft[d][v].d;
+      if (dir < 5)
+        gq[dir] = gi;
+      else if (dir < 20)
+        gdq[(dir - 5) / 5][(dir - 5) % 5] = gi;
+      else
+        gmu = gi;
+    }
+  }
+  mured[tid] = gmu;
+
+  // trace transpose summed over the cell's points (group butterfly)
+  double val[NOP2];
+#pragma unroll
+  for (int o = 0; o < NOP2; ++o) {
+    double c = 0.0;
+    if (o < NC) {
+      const int v = o / NM, mm = o % NM;
+      const int e0 = mode_exp(mm, 0), e1 = mode_exp(mm, 1), e2 = mode_exp(mm, 2);
+      c = (L1[0][e0] * L1[1][e1] * L1[2][e2]) * gq[v] + sc[0] * (dL1[0][e0] * L1[1][e1] * L1[2][e2]) * gdq[0][v] +
+          sc[1] * (L1[0][e0] * dL1[1][e1] * L1[2][e2]) * gdq[1][v] +
+          sc[2] * (L1[0][e0] * L1[1][e1] * dL1[2][e2]) * gdq[2][v];
+    }
+    val[o] = c;
+  }
+  double outv[NOP2 / PG];
+  group_reduce<NOP2, PG>(val, outv, lg);
+#pragma unroll
+  for (int r = 0; r < NOP2 / PG; ++r) red[cb][(NOP2 / PG) * lg + r] = outv[r];
+  __syncthreads();
+
+  // add the faces' cotangents and the pass-through terms
+  for (int o = tid; o < CB * NC; o += nthr) {
+    const int cc = o % CB, comp = o / CB, i = i0 + cc;
+    if (i >= nx) continue;
+    const size_t cell = row + i, idx = (size_t)comp * nc + cell;
+    double s = red[cc][comp];
+#pragma unroll
+    for (int D = 0; D < 3; ++D) {
+      size_t up;
+      if (D == 0)
+        up = row + wrapm(i + 1, nx);
+      else if (D == 1)
+        up = ((size_t)k * ny + wrapm(j + 1, ny)) * nx + i;
+      else
+        up = ((size_t)wrapm(k + 1, nz) * ny + j) * nx + i;
+      s += io.H[(((size_t)D * 2 + 1) * NC + comp) * nc + cell];  // this cell is right of its low face
+      s += io.H[(((size_t)D * 2 + 0) * NC + comp) * nc + up];    // and left of its high face
+    }
+    if (io.addA) s += io.addA[idx];
+    if (io.addB) s += io.addB[idx];
+    io.out[idx] = s;
+  }
+  if (tid == 0) {
+    double sm = 0.0;
+    for (int t = 0; t < nthr; ++t) sm += mured[t];
+    const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    io.mu_part[mu_offset + blk] = sm;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gradient of E_k = 1/(rho0 |Omega|) sum w |K| |m|^2/(2 rho) (n_q^3 points):
+// dE/dQ[v][n] = 1/(rho0 |Omega|) sum_p w |K| B_n(p) de/dq_v, with
+// de/drho = -|m|^2/(2 rho^2), de/dm_d = m_d / rho, de/drhoE = 0.
+// ---------------------------------------------------------------------------
+template <int ORDER, int NQ>
+__global__ void __launch_bounds__(RED_THREADS) k_ek_vjp(const double* __restrict__ Q, long long nc, double scale,
+                                                        double* __restrict__ out) {
+  constexpr int NM = n_modes(ORDER);
+  for (long long c = (long long)blockIdx.x * RED_THREADS + threadIdx.x; c < nc; c += (long long)gridDim.x * RED_THREADS) {
+    double co[4][NM], g[5][NM];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int mm = 0; mm < NM; ++mm) co[v][mm] = Q[(size_t)(v * NM + mm) * nc + c];
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int mm = 0; mm < NM; ++mm) g[v][mm] = 0.0;
+#pragma unroll
+    for (int a = 0; a < NQ; ++a)
+#pragma unroll
+      for (int b = 0; b < NQ; ++b)
+#pragma unroll
+        for (int cz = 0; cz < NQ; ++cz) {
+          double qv[4] = {0, 0, 0, 0}, B[NM];
+#pragma unroll
+          for (int mm = 0; mm < NM; ++mm) {
+            B[mm] = leg<double>(mode_exp(mm, 0), gauss_x(NQ, a)) * leg<double>(mode_exp(mm, 1), gauss_x(NQ, b)) *
+                    leg<double>(mode_exp(mm, 2), gauss_x(NQ, cz));
+#pragma unroll
+            for (int v = 0; v < 4; ++v) qv[v] += co[v][mm] * B[mm];
+          }
+          const double wq = gauss_w(NQ, a) * gauss_w(NQ, b) * gauss_w(NQ, cz) * scale;
+          const double ir = 1.0 / qv[0];
+          const double m2 = qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
+          const double de[4] = {-0.5 * m2 * ir * ir, qv[1] * ir, qv[2] * ir, qv[3] * ir};
+#pragma unroll
+          for (int mm = 0; mm < NM; ++mm)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) g[v][mm] += wq * B[mm] * de[v];
+        }
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int mm = 0; mm < NM; ++mm) out[(size_t)(v * NM + mm) * nc + c] = g[v][mm];
+  }
+}
+
+// sum of the viscosity-cotangent partials (fixed order), added to *acc
+__global__ void k_mu_sum(const double* __restrict__ part, long long n, double* __restrict__ acc) {
+  __shared__ double sh[RED_THREADS];
+  double s = 0.0;
+  for (long long b = threadIdx.x; b < n; b += RED_THREADS) s += part[b];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = RED_THREADS / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *acc += sh[0];
+}
+
+}  // namespace dghgks

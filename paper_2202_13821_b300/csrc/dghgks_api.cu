@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 
+#include "dg_adjoint.cuh"
 #include "dg_kernels.cuh"
 #include "dghgks.h"
 
@@ -37,6 +38,11 @@ struct dghgks_ctx {
   double* red = nullptr;   // reduction results (device)
   double* red_host = nullptr;  // pinned
   double* Qdev = nullptr;      // device state for dghgks_run_host
+  // adjoint scratch (FP64 contexts, allocated on first use)
+  double* adjH = nullptr;      // face cotangents [3][2][5 N_m][cells]
+  double* adjLam = nullptr;    // lambda* (state size)
+  double* adjMu = nullptr;     // viscosity partials
+  size_t adjMuN = 0;
   const Ops* ops = nullptr;
   int64_t launches = 0;
   // profiling: event pairs around launches
@@ -119,6 +125,10 @@ struct ProfScope {
 
 struct Ops {
   cudaError_t (*set_attrs)();
+  // adjoint of one residual (FP64 only; NULL for FP32-mixed)
+  cudaError_t (*adj_attrs)();
+  void (*vjp)(dghgks_ctx*, const double*, double, const AdjIO&, cudaStream_t);
+  void (*ek_vjp)(dghgks_ctx*, const double*, double, double*, cudaStream_t);
   // face pass on a state stored in FP64 (q_in_r = false) or in the flux precision
   void (*faces)(dghgks_ctx*, const void*, bool, double, cudaStream_t);
   // cell pass: MODE_RESIDUAL (Q, L, Lt), MODE_STAGE1 (Q^n), MODE_STAGE2 (Q^n updated in place)
@@ -201,6 +211,11 @@ struct Impl {
     c->launches += 1;
   }
 
+  static void ek_vjp(dghgks_ctx* c, const double* Q, double scale, double* out, cudaStream_t s) {
+    k_ek_vjp<ORDER, NQ><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, c->ncell, scale, out);
+    c->launches += 1;
+  }
+
   static void ek(dghgks_ctx* c, const double* Q, cudaStream_t s) {
     ProfScope ps(c, 6, s);
     k_ek_part<ORDER, NQ><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, c->ncell, c->part);
@@ -208,8 +223,47 @@ struct Impl {
   }
 };
 
-#define DG_OPS(R, O, N) \
-  Ops { &Impl<R, O, N>::set_attrs, &Impl<R, O, N>::faces, &Impl<R, O, N>::cell, &Impl<R, O, N>::ek, sizeof(R) }
+// adjoint dispatch (FP64)
+template <int ORDER, int NQ>
+struct AdjImpl {
+  static cudaError_t set_attrs() {
+    cudaError_t e = cudaSuccess;
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    const int fb = (int)FaceAdjSmem<ORDER, NQ>::bytes, cb = (int)CellAdjSmem<ORDER, NQ>::bytes;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 0>, a, fb);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 1>, a, fb);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 2>, a, fb);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cell_vjp<ORDER, NQ>, a, cb);
+    return e;
+  }
+  static void vjp(dghgks_ctx* c, const double* Q, double dt, const AdjIO& io, cudaStream_t s) {
+    const GasPar<double> g = gas_par<double>(c, dt);
+    const MeshDev m = mesh_dev(c);
+    const dim3 fgrid((c->n[0] + FB - 1) / FB, c->n[1], c->n[2]), fblock(FB * NQ * NQ);
+    const size_t fblocks = (size_t)fgrid.x * fgrid.y * fgrid.z;
+    const size_t fbytes = FaceAdjSmem<ORDER, NQ>::bytes;
+    k_face_vjp<ORDER, NQ, 0><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 0 * fblocks);
+    k_face_vjp<ORDER, NQ, 1><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 1 * fblocks);
+    k_face_vjp<ORDER, NQ, 2><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 2 * fblocks);
+    using LY = CellLayout<ORDER, NQ>;
+    const dim3 cgrid((c->n[0] + LY::CB - 1) / LY::CB, c->n[1], c->n[2]), cblock(LY::WARPS * 32);
+    k_cell_vjp<ORDER, NQ><<<cgrid, cblock, CellAdjSmem<ORDER, NQ>::bytes, s>>>(Q, g, m, io, 3 * fblocks);
+    c->launches += 4;
+  }
+};
+
+template <class R, int O, int N>
+constexpr Ops make_ops() {
+  return Ops{&Impl<R, O, N>::set_attrs,
+             sizeof(R) == 8 ? &AdjImpl<O, N>::set_attrs : nullptr,
+             sizeof(R) == 8 ? &AdjImpl<O, N>::vjp : nullptr,
+             &Impl<R, O, N>::ek_vjp,
+             &Impl<R, O, N>::faces,
+             &Impl<R, O, N>::cell,
+             &Impl<R, O, N>::ek,
+             sizeof(R)};
+}
+#define DG_OPS(R, O, N) make_ops<R, O, N>()
 
 const Ops kOps64_1_2 = DG_OPS(double, 1, 2);
 const Ops kOps64_2_2 = DG_OPS(double, 2, 2);
@@ -355,6 +409,9 @@ void dghgks_destroy(dghgks_ctx* c) {
   cudaFree(c->part);
   cudaFree(c->red);
   cudaFree(c->Qdev);
+  cudaFree(c->adjH);
+  cudaFree(c->adjLam);
+  cudaFree(c->adjMu);
   if (c->red_host) cudaFreeHost(c->red_host);
   delete c;
 }
@@ -562,6 +619,97 @@ int dghgks_profile_read(dghgks_ctx* c, double* ms, int64_t* launches) {
     launches[c->prof_kind[i]] += 1;
   }
   return DGHGKS_OK;
+}
+
+static int adj_prepare(dghgks_ctx* c) {
+  if (!c->ops->vjp) return fail(c, DGHGKS_EUNSUP, "the adjoint needs an FP64 context");
+  if (c->adjH) return DGHGKS_OK;
+  const size_t nc = (size_t)c->ncell;
+  const size_t state = sizeof(double) * 5 * (size_t)c->nm * nc;
+  const size_t fblocks = (size_t)((c->n[0] + FB - 1) / FB) * c->n[1] * c->n[2];
+  const size_t cblocks = (size_t)((c->n[0] + 7) / 8) * c->n[1] * c->n[2];  // cell CTAs own >= 8 cells
+  c->adjMuN = 3 * fblocks + cblocks;
+  int rc = cuda_check(c, c->ops->adj_attrs(), "adjoint attributes");
+  if (!rc) rc = cuda_check(c, cudaMalloc(&c->adjH, 6 * state), "cudaMalloc(face cotangents)");
+  if (!rc) rc = cuda_check(c, cudaMalloc(&c->adjLam, state), "cudaMalloc(adjoint state)");
+  if (!rc) rc = cuda_check(c, cudaMalloc(&c->adjMu, sizeof(double) * c->adjMuN), "cudaMalloc(adjoint partials)");
+  if (rc) {
+    cudaFree(c->adjH);
+    cudaFree(c->adjLam);
+    cudaFree(c->adjMu);
+    c->adjH = c->adjLam = c->adjMu = nullptr;
+  }
+  return rc;
+}
+
+// one residual VJP with the viscosity cotangent added to *dmu
+static int adj_vjp(dghgks_ctx* c, const double* Q, double dt, AdjIO io, double* dmu, cudaStream_t s) {
+  io.H = c->adjH;
+  io.mu_part = c->adjMu;
+  if (int rc = cuda_check(c, cudaMemsetAsync(c->adjMu, 0, sizeof(double) * c->adjMuN, s), "memset")) return rc;
+  c->ops->vjp(c, Q, dt, io, s);
+  k_mu_sum<<<1, RED_THREADS, 0, s>>>(c->adjMu, (long long)c->adjMuN, dmu);
+  c->launches += 1;
+  return after_launch(c, "adjoint launch");
+}
+
+int dghgks_residual_vjp(dghgks_ctx* c, const double* Q, double dt, const double* lamL, const double* lamLt,
+                        double* lamQ, double* dmu, void* stream) {
+  if (!c) return DGHGKS_EARG;
+  if (!Q || !lamL || !lamLt || !lamQ || !dmu) return fail(c, DGHGKS_EARG, "NULL argument");
+  if (!(dt > 0)) return fail(c, DGHGKS_EARG, "dt must be > 0");
+  if (lamQ == Q || lamQ == lamL || lamQ == lamLt) return fail(c, DGHGKS_EARG, "lamQ must not alias the inputs");
+  if (int rc = adj_prepare(c)) return rc;
+  AdjIO io{};
+  io.lamA = lamL;
+  io.lamB = lamLt;
+  io.cLA = 1.0;
+  io.cLB = 0.0;
+  io.cTA = 0.0;
+  io.cTB = 1.0;
+  io.out = lamQ;
+  return adj_vjp(c, Q, dt, io, dmu, static_cast<cudaStream_t>(stream));
+}
+
+int dghgks_adjoint_step(dghgks_ctx* c, const double* Qn, const double* lam_next, double dt, double* lam_n,
+                        double* dJ_dmu, void* stream) {
+  if (!c) return DGHGKS_EARG;
+  if (!Qn || !lam_next || !lam_n || !dJ_dmu) return fail(c, DGHGKS_EARG, "NULL argument");
+  if (!(dt > 0)) return fail(c, DGHGKS_EARG, "dt must be > 0");
+  if (lam_n == Qn) return fail(c, DGHGKS_EARG, "lam_n must not alias Qn");
+  if (int rc = adj_prepare(c)) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // recompute Q* from the checkpoint (one forward stage)
+  c->ops->faces(c, Qn, false, dt, s);
+  c->ops->cell(c, MODE_STAGE1, const_cast<double*>(Qn), nullptr, nullptr, dt, s);
+  const double* Qs = static_cast<const double*>(c->Qs);
+  // stage 2 at Q*: only L_t(Q*) enters Q^{n+1}, with dt^2/3
+  AdjIO io2{};
+  io2.lamA = lam_next;
+  io2.cTA = dt * dt / 3.0;
+  io2.out = c->adjLam;
+  if (int rc = adj_vjp(c, Qs, dt, io2, dJ_dmu, s)) return rc;
+  // stage 1 at Q^n: L with dt (direct) and dt/2 (through Q*), L_t with dt^2/6 and dt^2/8
+  AdjIO io1{};
+  io1.lamA = lam_next;
+  io1.lamB = c->adjLam;
+  io1.cLA = dt;
+  io1.cLB = 0.5 * dt;
+  io1.cTA = dt * dt / 6.0;
+  io1.cTB = dt * dt / 8.0;
+  io1.out = lam_n;
+  io1.addA = lam_next;
+  io1.addB = c->adjLam;
+  return adj_vjp(c, Qn, dt, io1, dJ_dmu, s);
+}
+
+int dghgks_kinetic_energy_vjp(dghgks_ctx* c, const double* Q, double rho0, double* dEk_dQ, void* stream) {
+  if (!c) return DGHGKS_EARG;
+  if (!Q || !dEk_dQ || dEk_dQ == Q) return fail(c, DGHGKS_EARG, "bad argument");
+  if (!(rho0 > 0)) return fail(c, DGHGKS_EARG, "rho0 must be > 0");
+  const double omega = c->vol * (double)c->ncell;
+  c->ops->ek_vjp(c, Q, c->vol / (rho0 * omega), dEk_dQ, static_cast<cudaStream_t>(stream));
+  return after_launch(c, "E_k VJP launch");
 }
 
 int dghgks_status(dghgks_ctx* c, void* stream) {
