@@ -135,6 +135,12 @@ int dghgks_totals(dghgks_ctx* ctx, const double* Q, double* out, void* stream);
  * host memory. */
 int dghgks_kinetic_energy(dghgks_ctx* ctx, const double* Q, double rho0, double* Ek, void* stream);
 
+/* Enstrophy-based dissipation rate (Sec. 5.3):
+ *   eps(zeta) = 2 mu / (rho0 |Omega|) int rho |omega|^2 / 2,  omega = curl U,
+ * with the context's mu, by the n_q^3 cell Gauss rule, in FP64.
+ * Synchronises; eps is host memory. */
+int dghgks_enstrophy_dissipation(dghgks_ctx* ctx, const double* Q, double rho0, double* eps, void* stream);
+
 /* L2 norm over the domain of the difference of two modal states, variable
  * var, in FP64 (orthogonal basis: sum_cells sum_n M_nn (A_n - B_n)^2).
  * Synchronises; out is host memory. */

@@ -157,6 +157,16 @@ def kinetic_energy(pb: Problem, Q: np.ndarray, rho0: float = 1.0) -> float:
     return e.value
 
 
+def enstrophy_dissipation(pb: Problem, Q: np.ndarray, rho0: float = 1.0) -> float:
+    """eps(zeta) = 2 mu / (rho0 |Omega|) int rho |curl U|^2 / 2 (Sec. 5.3)."""
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    e = ctypes.c_double()
+    c = pb.cfg()
+    _check(lib().orc_enstrophy_dissipation(ctypes.byref(c), _p(Q), ctypes.c_double(rho0), ctypes.byref(e)),
+           "enstrophy_dissipation")
+    return e.value
+
+
 IC_ADVECTION = 1
 IC_TGV = 2
 

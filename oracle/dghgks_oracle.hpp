@@ -863,6 +863,33 @@ inline T kinetic_energy(const Grid& G, const T* Q, double rho0) {
   return s / (rho0 * vol * G.cells());
 }
 
+// Enstrophy-based dissipation of Sec. 5.3:
+// eps(zeta) = 2 mu / (rho_0 |Omega|) int rho |curl U|^2 / 2, n_q^3 cell Gauss rule.
+inline double enstrophy_dissipation(const Grid& G, const double* Q, double mu, double rho0) {
+  const std::vector<Mode> md = mode_list(G.order);
+  double gx[8], gw[8];
+  gauss_rule(G.nq, gx, gw);
+  const double vol = G.h(0) * G.h(1) * G.h(2);
+  double s = 0.0;
+  for (int k = 0; k < G.n[2]; ++k)
+    for (int j = 0; j < G.n[1]; ++j)
+      for (int i = 0; i < G.n[0]; ++i)
+        for (int a = 0; a < G.nq; ++a)
+          for (int b = 0; b < G.nq; ++b)
+            for (int c = 0; c < G.nq; ++c) {
+              const double r[3] = {gx[a], gx[b], gx[c]};
+              double q[5], dq[3][5];
+              trace(G, md, Q, i, j, k, r, q, dq);
+              // velocity gradient dU_e/dx_d = (dm_e/dx_d - U_e drho/dx_d) / rho
+              double du[3][3];
+              for (int d = 0; d < 3; ++d)
+                for (int e = 0; e < 3; ++e) du[d][e] = (dq[d][1 + e] - q[1 + e] / q[0] * dq[d][0]) / q[0];
+              const double w[3] = {du[1][2] - du[2][1], du[2][0] - du[0][2], du[0][1] - du[1][0]};
+              s += gw[a] * gw[b] * gw[c] * vol * 0.5 * q[0] * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+            }
+  return 2.0 * mu * s / (rho0 * vol * G.cells());
+}
+
 // Initial conditions of Sec. 5 as conservative variables at a point.
 // ic 1: density advection rho = 1 + A sin(pi (x+y+z - 3t)), U=V=W=1, p=1
 //       (par[0] = A, t = par[1]).

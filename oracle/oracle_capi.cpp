@@ -187,6 +187,13 @@ int orc_kinetic_energy(const orc_cfg* c, const double* Q, double rho0, double* E
   return 0;
 }
 
+int orc_enstrophy_dissipation(const orc_cfg* c, const double* Q, double rho0, double* eps) {
+  orc::Grid G;
+  if (!make_grid(c, G)) return -1;
+  *eps = orc::enstrophy_dissipation(G, Q, c->mu, rho0);
+  return 0;
+}
+
 int orc_project(const orc_cfg* c, int ic, const double* par, double* Q) {
   orc::Grid G;
   if (!make_grid(c, G) || (ic != 1 && ic != 2)) return -1;

@@ -58,6 +58,7 @@ _SIGS = {
     "dghgks_totals": (_I, [_VP, _VP, _DP, _VP]),
     "dghgks_kinetic_energy": (_I, [_VP, _VP, _D, _DP, _VP]),
     "dghgks_l2_diff": (_I, [_VP, _VP, _VP, _I, _DP, _VP]),
+    "dghgks_enstrophy_dissipation": (_I, [_VP, _VP, _D, _DP, _VP]),
     "dghgks_status": (_I, [_VP, _VP]),
     "dghgks_launch_count": (ctypes.c_int64, [_VP]),
     "dghgks_gauss_rule": (_I, [_I, _DP, _DP]),
@@ -174,6 +175,12 @@ def dghgks_totals(ctx, Q, stream=None) -> np.ndarray:
 def dghgks_kinetic_energy(ctx, Q, rho0: float = 1.0, stream=None) -> float:
     e = ctypes.c_double()
     _check(ctx, load().dghgks_kinetic_energy(ctx, _ptr(Q), rho0, ctypes.byref(e), _stream(stream)))
+    return e.value
+
+
+def dghgks_enstrophy_dissipation(ctx, Q, rho0: float = 1.0, stream=None) -> float:
+    e = ctypes.c_double()
+    _check(ctx, load().dghgks_enstrophy_dissipation(ctx, _ptr(Q), rho0, ctypes.byref(e), _stream(stream)))
     return e.value
 
 
@@ -297,6 +304,9 @@ class Solver:
 
     def kinetic_energy(self, Q, rho0=1.0, stream=None):
         return dghgks_kinetic_energy(self.ctx, Q, rho0, stream)
+
+    def enstrophy_dissipation(self, Q, rho0=1.0, stream=None):
+        return dghgks_enstrophy_dissipation(self.ctx, Q, rho0, stream)
 
     def l2_diff(self, A, B, var=0, stream=None):
         return dghgks_l2_diff(self.ctx, A, B, var, stream)

@@ -9,7 +9,10 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SO = os.path.join(HERE, "libdghgks.so")
-SOURCES = [os.path.join(HERE, "csrc", "dghgks_api.cu"), os.path.join(HERE, "csrc", "dghgks_static.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "dghgks_api.cu"), os.path.join(HERE, "csrc", "dghgks_static.cu"),
+           os.path.join(HERE, "csrc", "dghgks_adjoint.cu")]
+# extra device-compiler options per source (see the header of dghgks_adjoint.cu)
+EXTRA = {"dghgks_adjoint.cu": ["-Xptxas", "-O1"]}
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc")) if f.endswith((".cu", ".cuh"))] + [
     os.path.join(ROOT, "include", "dghgks.h")]
 
@@ -59,11 +62,25 @@ def build(force: bool = False, verbose: bool = False) -> str:
     newest = max(os.path.getmtime(f) for f in DEPS if os.path.exists(f))
     if not force and os.path.exists(SO) and os.path.getmtime(SO) >= newest:
         return SO
-    cmd = [nvcc(), *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", SO + ".tmp", *SOURCES, "-lcudart"]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.run(cmd, check=True)
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    flags = [f for f in NVCC_FLAGS if f != "-shared"]
+    procs, objs = [], []
+    for src in SOURCES:
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        cmd = [nvcc(), *flags, *EXTRA.get(os.path.basename(src), []), "-I", os.path.join(ROOT, "include"), "-c",
+               "-o", obj, src]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append(subprocess.Popen(cmd))
+        objs.append(obj)
+    for pr in procs:
+        if pr.wait() != 0:
+            raise subprocess.CalledProcessError(pr.returncode, "nvcc")
+    link = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-Xcompiler", "-fPIC", "-o", SO + ".tmp",
+            *objs, "-lcudart"]
+    subprocess.run(link, check=True)
     os.replace(SO + ".tmp", SO)
     return SO
 

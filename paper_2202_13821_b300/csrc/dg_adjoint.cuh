@@ -18,6 +18,7 @@
 #pragma once
 #include <cmath>
 
+#include "adjoint.h"
 #include "dg_kernels.cuh"
 
 namespace dghgks {
@@ -57,19 +58,22 @@ DG_HD DualD erfc(DualD a) {
   return DualD(::erfc(a.v), -1.12837916709551257390 * ::exp(-a.v * a.v) * a.d);
 }
 
-// Adjoint scratch of one stage: face cotangents H[D][side][comp][face]
-// (side 0 = left cell of the face, 1 = right cell; comp = v * NM + n).
-struct AdjIO {
-  const double* lamA;  // first cotangent input (state layout)
-  const double* lamB;  // second cotangent input (may be NULL)
-  double cLA, cLB;     // lambda_L  = cLA lamA + cLB lamB
-  double cTA, cTB;     // lambda_Lt = cTA lamA + cTB lamB
-  double* H;           // face cotangents
-  double* out;         // cotangent of Q (state layout)
-  const double* addA;  // out = addA + addB + J^T lambda (either may be NULL)
-  const double* addB;
-  double* mu_part;     // per-CTA partial sums of the viscosity cotangent
-};
+// sums += constant side sums (zero tangents)
+DG_HD void add_sums(SideSums<DualD>& a, const SideSums<double>& b) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    a.Q0[k] += DualD(b.Q0[k]);
+    a.V4[k] += DualD(b.V4[k]);
+    a.V5[k] += DualD(b.V5[k]);
+    a.V6[k] += DualD(b.V6[k]);
+    a.W5[k] += DualD(b.W5[k]);
+    a.W6[k] += DualD(b.W6[k]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) a.dQ0[i][k] += DualD(b.dQ0[i][k]);
+  }
+}
+
+
 
 template <int ORDER, int NQ>
 struct FaceAdjSmem {
@@ -184,7 +188,37 @@ __global__ void __launch_bounds__(FB* NQ* NQ)
     }
   }
 
-  // 41 directions: traces of both sides (q: 5, dq: 15 each) and mu
+  // 41 directions: traces of both sides (q: 5, dq: 15 each) and mu.  A
+  // direction seeds one side only, so the other side's sums are taken from a
+  // plain FP64 pass and only the seeded side (and the finish) runs in dual
+  // numbers.
+  const bool pr_fix = (gp.pr_fix != 0.0);
+  SideSums<double> s0[2];
+  double ql0[2][5], dql0[2][3][5];
+  {
+    const int ax[3] = {A0, A1, A2};
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      ql0[side][0] = q[side][0];
+      ql0[side][1] = q[side][1 + A0];
+      ql0[side][2] = q[side][1 + A1];
+      ql0[side][3] = q[side][1 + A2];
+      ql0[side][4] = q[side][4];
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii) {
+        dql0[side][ii][0] = dq[side][ax[ii]][0];
+        dql0[side][ii][1] = dq[side][ax[ii]][1 + A0];
+        dql0[side][ii][2] = dq[side][ax[ii]][1 + A1];
+        dql0[side][ii][3] = dq[side][ax[ii]][1 + A2];
+        dql0[side][ii][4] = dq[side][ax[ii]][4];
+      }
+      iface_zero(s0[side]);
+    }
+    iface_side<double, +1>(ql0[0], dql0[0], gp, pr_fix, s0[0]);
+    iface_side<double, -1>(ql0[1], dql0[1], gp, pr_fix, s0[1]);
+  }
+  // local index of a global momentum component
+  const int loc[3] = {(0 - A0 + 3) % 3, (1 - A0 + 3) % 3, (2 - A0 + 3) % 3};
   double gmu = 0.0;
   GasPar<DualD> gd;
   gd.K = DualD(gp.K);
@@ -195,36 +229,31 @@ __global__ void __launch_bounds__(FB* NQ* NQ)
   gd.inv_dt = DualD(gp.inv_dt);
   for (int dir = 0; dir < 41; ++dir) {
     gd.mu = DualD(gp.mu, dir == 40 ? 1.0 : 0.0);
-    const bool pr_fix = (gp.pr_fix != 0.0);
+    const int side = dir < 20 ? 0 : 1;
+    const int r = dir - 20 * side;  // 0..4: q[v]; 5..19: dq[d][v] (global d, v)
     SideSums<DualD> sums;
-    iface_zero(sums);
+    if (dir < 40) {
+      // seed the input in the local frame: global variable v -> local component
+      const int v = r < 5 ? r : (r - 5) % 5;
+      const int lv = (v >= 1 && v <= 3) ? 1 + loc[v - 1] : v;
+      const int li = r < 5 ? -1 : loc[(r - 5) / 5];  // local derivative index
+      DualD ql[5], dql[3][5];
 #pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      DualD ql[5], dql[3][5], qg[5], dqg[3][5];
+      for (int k2 = 0; k2 < 5; ++k2) {
+        ql[k2] = DualD(ql0[side][k2], (li < 0 && k2 == lv) ? 1.0 : 0.0);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        qg[v] = DualD(q[side][v], dir == side * 20 + v ? 1.0 : 0.0);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) dqg[d][v] = DualD(dq[side][d][v], dir == side * 20 + 5 + d * 5 + v ? 1.0 : 0.0);
+        for (int ii = 0; ii < 3; ++ii) dql[ii][k2] = DualD(dql0[side][ii][k2], (ii == li && k2 == lv) ? 1.0 : 0.0);
       }
-      const int ax[3] = {A0, A1, A2};
-      ql[0] = qg[0];
-      ql[1] = qg[1 + A0];
-      ql[2] = qg[1 + A1];
-      ql[3] = qg[1 + A2];
-      ql[4] = qg[4];
-#pragma unroll
-      for (int ii = 0; ii < 3; ++ii) {
-        dql[ii][0] = dqg[ax[ii]][0];
-        dql[ii][1] = dqg[ax[ii]][1 + A0];
-        dql[ii][2] = dqg[ax[ii]][1 + A1];
-        dql[ii][3] = dqg[ax[ii]][1 + A2];
-        dql[ii][4] = dqg[ax[ii]][4];
-      }
+      iface_zero(sums);
       if (side == 0)
         iface_side<DualD, +1>(ql, dql, gd, pr_fix, sums);
       else
         iface_side<DualD, -1>(ql, dql, gd, pr_fix, sums);
+      add_sums(sums, s0[1 - side]);
+    } else {
+      iface_zero(sums);
+      add_sums(sums, s0[0]);
+      add_sums(sums, s0[1]);
     }
     DualD Fl[5], Ftl[5];
     iface_finish(sums, gd, Fl, Ftl);
@@ -283,7 +312,8 @@ struct CellAdjSmem {
   static constexpr int NOP2 = (NC + LY::PG - 1) / LY::PG * LY::PG;
   static constexpr size_t coef = sizeof(double) * NC * CB;
   static constexpr size_t red = sizeof(double) * CB * NOP2;
-  static constexpr size_t bytes = 3 * coef + red + sizeof(double) * LY::WARPS * 32;
+  static constexpr size_t gsc = sizeof(double) * 20 * LY::WARPS * 32;
+  static constexpr size_t bytes = 3 * coef + red + sizeof(double) * LY::WARPS * 32 + gsc;
 };
 
 template <int ORDER, int NQ>
@@ -299,6 +329,8 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
   double(*cmuT)[CB] = reinterpret_cast<double(*)[CB]>(smem_raw + 2 * S::coef);
   double(*red)[NOP2] = reinterpret_cast<double(*)[NOP2]>(smem_raw + 3 * S::coef);
   double* mured = reinterpret_cast<double*>(smem_raw + 3 * S::coef + S::red);
+  double(*gsc)[LY::WARPS * 32] =
+      reinterpret_cast<double(*)[LY::WARPS * 32]>(smem_raw + 3 * S::coef + S::red + sizeof(double) * LY::WARPS * 32);
 
   const int tid = threadIdx.x, nthr = LY::WARPS * 32;
   const int lane = tid & 31, lg = lane % PG;
@@ -369,8 +401,9 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
     }
   }
 
-  // 21 directions: q (5), dq (15), mu
-  double gq[5] = {0, 0, 0, 0, 0}, gdq[3][5] = {{0}}, gmu = 0.0;
+  // 21 directions: q (5), dq (15), mu; the input cotangents go through
+  // shared memory (indexed by direction) to keep the loop body small
+  double gmu = 0.0;
   GasPar<DualD> gd;
   gd.K = DualD(gp.K);
   gd.gm1 = DualD(gp.gm1);
@@ -378,8 +411,10 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
   gd.pr_fix = DualD(gp.pr_fix);
   gd.dt = DualD(gp.dt);
   gd.inv_dt = DualD(gp.inv_dt);
-  if (active) {
-    for (int dir = 0; dir < 21; ++dir) {
+  #pragma unroll 1
+  for (int dir = 0; dir < 21; ++dir) {
+    double gi = 0.0;
+    if (active) {
       gd.mu = DualD(gp.mu, dir == 20 ? 1.0 : 0.0);
       DualD qd[5], dqd[3][5], F[3][5], Ft[3][5];
 #pragma unroll
@@ -389,39 +424,47 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
         for (int d = 0; d < 3; ++d) dqd[d][v] = DualD(dq[d][v], dir == 5 + d * 5 + v ? 1.0 : 0.0);
       }
       interior_flux(qd, dqd, gd, F, Ft);
-      double gi = 0.0;
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int v = 0; v < 5; ++v) gi += lF[d][v] * F[d][v].d + lT[d][v] * Ft[d][v].d;
-      if (dir < 5)
-        gq[dir] = gi;
-      else if (dir < 20)
-        gdq[(dir - 5) / 5][(dir - 5) % 5] = gi;
-      else
-        gmu = gi;
     }
+    if (dir < 20)
+      gsc[dir][tid] = gi;
+    else
+      gmu = gi;
+  }
+  double gq[5], gdq[3][5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    gq[v] = gsc[v][tid];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gdq[d][v] = gsc[5 + d * 5 + v][tid];
   }
   mured[tid] = gmu;
 
-  // trace transpose summed over the cell's points (group butterfly)
-  double val[NOP2];
+  // trace transpose summed over the cell's points (group butterfly), PG
+  // outputs at a time: lane lg ends with output c0 + lg of each chunk
 #pragma unroll
-  for (int o = 0; o < NOP2; ++o) {
-    double c = 0.0;
-    if (o < NC) {
-      const int v = o / NM, mm = o % NM;
-      const int e0 = mode_exp(mm, 0), e1 = mode_exp(mm, 1), e2 = mode_exp(mm, 2);
-      c = (L1[0][e0] * L1[1][e1] * L1[2][e2]) * gq[v] + sc[0] * (dL1[0][e0] * L1[1][e1] * L1[2][e2]) * gdq[0][v] +
-          sc[1] * (L1[0][e0] * dL1[1][e1] * L1[2][e2]) * gdq[1][v] +
-          sc[2] * (L1[0][e0] * L1[1][e1] * dL1[2][e2]) * gdq[2][v];
+  for (int c0 = 0; c0 < NOP2; c0 += PG) {
+    double val[PG];
+#pragma unroll
+    for (int oo = 0; oo < PG; ++oo) {
+      const int o = c0 + oo;
+      double c = 0.0;
+      if (o < NC) {
+        const int v = o / NM, mm = o % NM;
+        const int e0 = mode_exp(mm, 0), e1 = mode_exp(mm, 1), e2 = mode_exp(mm, 2);
+        c = (L1[0][e0] * L1[1][e1] * L1[2][e2]) * gq[v] + sc[0] * (dL1[0][e0] * L1[1][e1] * L1[2][e2]) * gdq[0][v] +
+            sc[1] * (L1[0][e0] * dL1[1][e1] * L1[2][e2]) * gdq[1][v] +
+            sc[2] * (L1[0][e0] * L1[1][e1] * dL1[2][e2]) * gdq[2][v];
+      }
+      val[oo] = c;
     }
-    val[o] = c;
+    double outv[1];
+    group_reduce<PG, PG>(val, outv, lg);
+    red[cb][c0 + lg] = outv[0];
   }
-  double outv[NOP2 / PG];
-  group_reduce<NOP2, PG>(val, outv, lg);
-#pragma unroll
-  for (int r = 0; r < NOP2 / PG; ++r) red[cb][(NOP2 / PG) * lg + r] = outv[r];
   __syncthreads();
 
   // add the faces' cotangents and the pass-through terms

@@ -548,6 +548,56 @@ __global__ void __launch_bounds__(RED_THREADS) k_ek_part(const double* __restric
   block_reduce_store<1>(acc, part);
 }
 
+// Enstrophy integral sum_cells sum_p w |K| rho |omega|^2 / 2 at the n_q^3
+// cell points (Sec. 5.3): omega = curl U, grad U = (grad m - U grad rho)/rho.
+template <int ORDER, int NQ>
+__global__ void __launch_bounds__(RED_THREADS) k_enstrophy_part(const double* __restrict__ Q, long long nc,
+                                                                double sx, double sy, double sz,
+                                                                double* __restrict__ part) {
+  constexpr int NM = n_modes(ORDER);
+  double acc[1] = {0};
+  const double sc[3] = {sx, sy, sz};
+  for (long long c = (long long)blockIdx.x * RED_THREADS + threadIdx.x; c < nc; c += (long long)gridDim.x * RED_THREADS) {
+    double co[4][NM];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int mm = 0; mm < NM; ++mm) co[v][mm] = Q[(size_t)(v * NM + mm) * nc + c];
+#pragma unroll
+    for (int a = 0; a < NQ; ++a)
+#pragma unroll
+      for (int b = 0; b < NQ; ++b)
+#pragma unroll
+        for (int cz = 0; cz < NQ; ++cz) {
+          const double x[3] = {gauss_x(NQ, a), gauss_x(NQ, b), gauss_x(NQ, cz)};
+          double q[4] = {0, 0, 0, 0}, g[3][4] = {{0}};
+#pragma unroll
+          for (int mm = 0; mm < NM; ++mm) {
+            const int e[3] = {mode_exp(mm, 0), mode_exp(mm, 1), mode_exp(mm, 2)};
+            const double P[3] = {leg<double>(e[0], x[0]), leg<double>(e[1], x[1]), leg<double>(e[2], x[2])};
+            const double dP[3] = {dleg<double>(e[0], x[0]), dleg<double>(e[1], x[1]), dleg<double>(e[2], x[2])};
+            const double B = P[0] * P[1] * P[2];
+            const double dB[3] = {dP[0] * P[1] * P[2], P[0] * dP[1] * P[2], P[0] * P[1] * dP[2]};
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              q[v] += co[v][mm] * B;
+#pragma unroll
+              for (int d = 0; d < 3; ++d) g[d][v] += co[v][mm] * dB[d] * sc[d];
+            }
+          }
+          const double ir = 1.0 / q[0];
+          double du[3][3];  // du[d][i] = d U_i / d x_d
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) du[d][i] = (g[d][1 + i] - q[1 + i] * ir * g[d][0]) * ir;
+          const double w0 = du[1][2] - du[2][1], w1 = du[2][0] - du[0][2], w2 = du[0][1] - du[1][0];
+          acc[0] += gauss_w(NQ, a) * gauss_w(NQ, b) * gauss_w(NQ, cz) * 0.5 * q[0] * (w0 * w0 + w1 * w1 + w2 * w2);
+        }
+  }
+  block_reduce_store<1>(acc, part);
+}
+
 template <int NV>
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const double* __restrict__ part, int nblocks,
                                                               double scale, double* __restrict__ out) {

@@ -1,0 +1,64 @@
+// Adjoint (VJP) kernels of the DG-HGKS residual and their launchers.  This
+// translation unit is compiled with -Xptxas -O1: at -O3 the register
+// allocation of the large dual-number kernels falls back to 32 registers and
+// spills tens of KB per thread; at -O1 they use the register file and spill
+// little.  The forward kernels stay in dghgks_api.cu at -O3.
+#include "adjoint.h"
+#include "dg_adjoint.cuh"
+
+namespace dghgks {
+
+namespace {
+constexpr int kRedBlocksAdj = 148 * 8;
+
+template <int ORDER, int NQ>
+cudaError_t attrs() {
+  cudaError_t e = cudaSuccess;
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  const int fb = (int)FaceAdjSmem<ORDER, NQ>::bytes, cb = (int)CellAdjSmem<ORDER, NQ>::bytes;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 0>, a, fb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 1>, a, fb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 2>, a, fb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cell_vjp<ORDER, NQ>, a, cb);
+  return e;
+}
+
+template <int ORDER, int NQ>
+void vjp(const double* Q, const GasPar<double>& g, const MeshDev& m, const AdjIO& io, cudaStream_t s) {
+  const dim3 fgrid((m.nx + FB - 1) / FB, m.ny, m.nz), fblock(FB * NQ * NQ);
+  const size_t fblocks = (size_t)fgrid.x * fgrid.y * fgrid.z;
+  const size_t fbytes = FaceAdjSmem<ORDER, NQ>::bytes;
+  k_face_vjp<ORDER, NQ, 0><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 0 * fblocks);
+  k_face_vjp<ORDER, NQ, 1><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 1 * fblocks);
+  k_face_vjp<ORDER, NQ, 2><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 2 * fblocks);
+  using LY = CellLayout<ORDER, NQ>;
+  const dim3 cgrid((m.nx + LY::CB - 1) / LY::CB, m.ny, m.nz), cblock(LY::WARPS * 32);
+  k_cell_vjp<ORDER, NQ><<<cgrid, cblock, CellAdjSmem<ORDER, NQ>::bytes, s>>>(Q, g, m, io, 3 * fblocks);
+}
+}  // namespace
+
+cudaError_t adjoint_set_attrs(int order, int nq) {
+  if (order == 1 && nq == 2) return attrs<1, 2>();
+  if (order == 2 && nq == 2) return attrs<2, 2>();
+  if (order == 2 && nq == 3) return attrs<2, 3>();
+  return cudaErrorInvalidValue;
+}
+
+void adjoint_vjp(int order, int nq, const double* Q, const GasPar<double>& g, const MeshDev& m, const AdjIO& io,
+                 cudaStream_t s) {
+  if (order == 1 && nq == 2) vjp<1, 2>(Q, g, m, io, s);
+  else if (order == 2 && nq == 2) vjp<2, 2>(Q, g, m, io, s);
+  else if (order == 2 && nq == 3) vjp<2, 3>(Q, g, m, io, s);
+}
+
+void adjoint_mu_sum(const double* part, long long n, double* acc, cudaStream_t s) {
+  k_mu_sum<<<1, RED_THREADS, 0, s>>>(part, n, acc);
+}
+
+void adjoint_ek_vjp(int order, int nq, const double* Q, long long nc, double scale, double* out, cudaStream_t s) {
+  if (order == 1 && nq == 2) k_ek_vjp<1, 2><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, nc, scale, out);
+  else if (order == 2 && nq == 2) k_ek_vjp<2, 2><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, nc, scale, out);
+  else if (order == 2 && nq == 3) k_ek_vjp<2, 3><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, nc, scale, out);
+}
+
+}  // namespace dghgks

@@ -8,7 +8,7 @@
 #include <cstring>
 #include <new>
 
-#include "dg_adjoint.cuh"
+#include "adjoint.h"
 #include "dg_kernels.cuh"
 #include "dghgks.h"
 
@@ -125,15 +125,12 @@ struct ProfScope {
 
 struct Ops {
   cudaError_t (*set_attrs)();
-  // adjoint of one residual (FP64 only; NULL for FP32-mixed)
-  cudaError_t (*adj_attrs)();
-  void (*vjp)(dghgks_ctx*, const double*, double, const AdjIO&, cudaStream_t);
-  void (*ek_vjp)(dghgks_ctx*, const double*, double, double*, cudaStream_t);
   // face pass on a state stored in FP64 (q_in_r = false) or in the flux precision
   void (*faces)(dghgks_ctx*, const void*, bool, double, cudaStream_t);
   // cell pass: MODE_RESIDUAL (Q, L, Lt), MODE_STAGE1 (Q^n), MODE_STAGE2 (Q^n updated in place)
   void (*cell)(dghgks_ctx*, int, double*, double*, double*, double, cudaStream_t);
   void (*ek)(dghgks_ctx*, const double*, cudaStream_t);
+  void (*enstrophy)(dghgks_ctx*, const double*, cudaStream_t);
   size_t r_size;
 };
 
@@ -211,8 +208,10 @@ struct Impl {
     c->launches += 1;
   }
 
-  static void ek_vjp(dghgks_ctx* c, const double* Q, double scale, double* out, cudaStream_t s) {
-    k_ek_vjp<ORDER, NQ><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, c->ncell, scale, out);
+  static void enstrophy(dghgks_ctx* c, const double* Q, cudaStream_t s) {
+    ProfScope ps(c, 6, s);
+    k_enstrophy_part<ORDER, NQ><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, c->ncell, 2.0 / c->h[0], 2.0 / c->h[1],
+                                                                    2.0 / c->h[2], c->part);
     c->launches += 1;
   }
 
@@ -223,44 +222,13 @@ struct Impl {
   }
 };
 
-// adjoint dispatch (FP64)
-template <int ORDER, int NQ>
-struct AdjImpl {
-  static cudaError_t set_attrs() {
-    cudaError_t e = cudaSuccess;
-    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    const int fb = (int)FaceAdjSmem<ORDER, NQ>::bytes, cb = (int)CellAdjSmem<ORDER, NQ>::bytes;
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 0>, a, fb);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 1>, a, fb);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 2>, a, fb);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cell_vjp<ORDER, NQ>, a, cb);
-    return e;
-  }
-  static void vjp(dghgks_ctx* c, const double* Q, double dt, const AdjIO& io, cudaStream_t s) {
-    const GasPar<double> g = gas_par<double>(c, dt);
-    const MeshDev m = mesh_dev(c);
-    const dim3 fgrid((c->n[0] + FB - 1) / FB, c->n[1], c->n[2]), fblock(FB * NQ * NQ);
-    const size_t fblocks = (size_t)fgrid.x * fgrid.y * fgrid.z;
-    const size_t fbytes = FaceAdjSmem<ORDER, NQ>::bytes;
-    k_face_vjp<ORDER, NQ, 0><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 0 * fblocks);
-    k_face_vjp<ORDER, NQ, 1><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 1 * fblocks);
-    k_face_vjp<ORDER, NQ, 2><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 2 * fblocks);
-    using LY = CellLayout<ORDER, NQ>;
-    const dim3 cgrid((c->n[0] + LY::CB - 1) / LY::CB, c->n[1], c->n[2]), cblock(LY::WARPS * 32);
-    k_cell_vjp<ORDER, NQ><<<cgrid, cblock, CellAdjSmem<ORDER, NQ>::bytes, s>>>(Q, g, m, io, 3 * fblocks);
-    c->launches += 4;
-  }
-};
-
 template <class R, int O, int N>
 constexpr Ops make_ops() {
   return Ops{&Impl<R, O, N>::set_attrs,
-             sizeof(R) == 8 ? &AdjImpl<O, N>::set_attrs : nullptr,
-             sizeof(R) == 8 ? &AdjImpl<O, N>::vjp : nullptr,
-             &Impl<R, O, N>::ek_vjp,
              &Impl<R, O, N>::faces,
              &Impl<R, O, N>::cell,
              &Impl<R, O, N>::ek,
+             &Impl<R, O, N>::enstrophy,
              sizeof(R)};
 }
 #define DG_OPS(R, O, N) make_ops<R, O, N>()
@@ -541,6 +509,24 @@ int dghgks_kinetic_energy(dghgks_ctx* c, const double* Q, double rho0, double* E
   return DGHGKS_OK;
 }
 
+int dghgks_enstrophy_dissipation(dghgks_ctx* c, const double* Q, double rho0, double* eps, void* stream) {
+  if (!c) return DGHGKS_EARG;
+  if (!Q || !eps) return fail(c, DGHGKS_EARG, "NULL argument");
+  if (!(rho0 > 0)) return fail(c, DGHGKS_EARG, "rho0 must be > 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->ops->enstrophy(c, Q, s);
+  const double omega = c->vol * (double)c->ncell;
+  k_reduce_final<1><<<1, RED_THREADS, 0, s>>>(c->part, kRedBlocks, 2.0 * c->mu * c->vol / (rho0 * omega), c->red);
+  c->launches += 1;
+  if (int rc = after_launch(c, "enstrophy launch")) return rc;
+  if (int rc = cuda_check(c, cudaMemcpyAsync(c->red_host, c->red, sizeof(double), cudaMemcpyDeviceToHost, s),
+                          "enstrophy copy"))
+    return rc;
+  if (int rc = cuda_check(c, cudaStreamSynchronize(s), "enstrophy sync")) return rc;
+  *eps = c->red_host[0];
+  return DGHGKS_OK;
+}
+
 int dghgks_l2_diff(dghgks_ctx* c, const double* A, const double* B, int var, double* out, void* stream) {
   if (!c) return DGHGKS_EARG;
   if (!A || !B || !out || var < 0 || var > 4) return fail(c, DGHGKS_EARG, "bad argument");
@@ -622,14 +608,14 @@ int dghgks_profile_read(dghgks_ctx* c, double* ms, int64_t* launches) {
 }
 
 static int adj_prepare(dghgks_ctx* c) {
-  if (!c->ops->vjp) return fail(c, DGHGKS_EUNSUP, "the adjoint needs an FP64 context");
+  if (c->precision != DGHGKS_FP64) return fail(c, DGHGKS_EUNSUP, "the adjoint needs an FP64 context");
   if (c->adjH) return DGHGKS_OK;
   const size_t nc = (size_t)c->ncell;
   const size_t state = sizeof(double) * 5 * (size_t)c->nm * nc;
   const size_t fblocks = (size_t)((c->n[0] + FB - 1) / FB) * c->n[1] * c->n[2];
   const size_t cblocks = (size_t)((c->n[0] + 7) / 8) * c->n[1] * c->n[2];  // cell CTAs own >= 8 cells
   c->adjMuN = 3 * fblocks + cblocks;
-  int rc = cuda_check(c, c->ops->adj_attrs(), "adjoint attributes");
+  int rc = cuda_check(c, adjoint_set_attrs(c->order, c->nq), "adjoint attributes");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->adjH, 6 * state), "cudaMalloc(face cotangents)");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->adjLam, state), "cudaMalloc(adjoint state)");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->adjMu, sizeof(double) * c->adjMuN), "cudaMalloc(adjoint partials)");
@@ -647,9 +633,9 @@ static int adj_vjp(dghgks_ctx* c, const double* Q, double dt, AdjIO io, double* 
   io.H = c->adjH;
   io.mu_part = c->adjMu;
   if (int rc = cuda_check(c, cudaMemsetAsync(c->adjMu, 0, sizeof(double) * c->adjMuN, s), "memset")) return rc;
-  c->ops->vjp(c, Q, dt, io, s);
-  k_mu_sum<<<1, RED_THREADS, 0, s>>>(c->adjMu, (long long)c->adjMuN, dmu);
-  c->launches += 1;
+  adjoint_vjp(c->order, c->nq, Q, gas_par<double>(c, dt), mesh_dev(c), io, s);
+  adjoint_mu_sum(c->adjMu, (long long)c->adjMuN, dmu, s);
+  c->launches += kAdjointLaunches + 1;
   return after_launch(c, "adjoint launch");
 }
 
@@ -708,7 +694,8 @@ int dghgks_kinetic_energy_vjp(dghgks_ctx* c, const double* Q, double rho0, doubl
   if (!Q || !dEk_dQ || dEk_dQ == Q) return fail(c, DGHGKS_EARG, "bad argument");
   if (!(rho0 > 0)) return fail(c, DGHGKS_EARG, "rho0 must be > 0");
   const double omega = c->vol * (double)c->ncell;
-  c->ops->ek_vjp(c, Q, c->vol / (rho0 * omega), dEk_dQ, static_cast<cudaStream_t>(stream));
+  adjoint_ek_vjp(c->order, c->nq, Q, c->ncell, c->vol / (rho0 * omega), dEk_dQ, static_cast<cudaStream_t>(stream));
+  c->launches += 1;
   return after_launch(c, "E_k VJP launch");
 }
 

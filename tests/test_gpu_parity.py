@@ -175,6 +175,8 @@ def test_totals_and_kinetic_energy(torch, api, orc):
     Qd = torch.from_numpy(Q).cuda()
     np.testing.assert_allclose(s.totals(Qd), orc.totals(pb, Q), rtol=1e-13, atol=1e-13)
     assert abs(s.kinetic_energy(Qd) - orc.kinetic_energy(pb, Q)) < 1e-14
+    e_gpu, e_orc = s.enstrophy_dissipation(Qd), orc.enstrophy_dissipation(pb, Q)
+    assert abs(e_gpu - e_orc) <= 1e-12 * abs(e_orc)
     # L2 difference through the mass matrix against a direct numpy evaluation
     Q2 = Q.copy()
     Q2[0] += 1e-3 * np.random.default_rng(1).standard_normal(Q2[0].shape)

@@ -91,6 +91,19 @@ def test_golden_orders_fixture_is_k_plus_1():
         assert abs(float(finest) - (int(k) + 1)) < 0.1
 
 
+def test_tgv_initial_enstrophy_dissipation(orc):
+    """omega of the initial field is (-cos x sin y sin z, -sin x cos y sin z, 2 sin x sin y cos z),
+    whose mean square is 3/4, so eps(zeta) = 2 mu (1/2)(3/4) = 0.75 mu at rho = 1 (Sec. 5.3)."""
+    mu = 1 / 1600
+    errs = []
+    for n in (8, 16):
+        pb = orc.Problem(order=2, nq=3, n=(n,) * 3, lo=(-math.pi,) * 3, hi=(math.pi,) * 3, mu=mu)
+        Q = orc.project(pb, orc.IC_TGV, (1.0, 1.0, 1.0 / (1.4 * 0.01), 0.0))
+        errs.append(abs(orc.enstrophy_dissipation(pb, Q) - 0.75 * mu) / (0.75 * mu))
+    # the gradient of the P2 projection converges at second order: 1.1e-2 at 8^3, 4.5e-3 at 16^3
+    assert errs[1] < 6e-3 and errs[1] < errs[0] / 2
+
+
 def test_tgv_initial_kinetic_energy(orc):
     pb = orc.Problem(order=2, nq=3, n=(8, 8, 8), lo=(-math.pi,) * 3, hi=(math.pi,) * 3, mu=1 / 1600, Pr=1.0)
     p0 = 1.0 / (1.4 * 0.01)
