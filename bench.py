@@ -229,6 +229,33 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def kernel_source_hash() -> str:
+    """Hash of the forward kernel sources; a profile summary is valid only for the same hash."""
+    import hashlib
+
+    h = hashlib.sha1()
+    for f in ("dg_kernels.cuh", "gks_point.cuh", "dg_tables.cuh"):
+        with open(os.path.join(ROOT, "paper_2202_13821_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(kernel: str, n: int):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary (profiles/<kernel>_*.md),
+    scaled to n^3 cells; None if no summary matches the current kernel sources."""
+    import glob
+    import re
+
+    cur = kernel_source_hash()
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md"))):
+        txt = open(f).read()
+        mh = re.search(r"source-hash:\s*([0-9a-f]+)", txt)
+        mb = re.search(r"dram-bytes-per-cell:\s*([0-9.eE+]+)", txt)
+        if mh and mb and mh.group(1) == cur:
+            return float(mb.group(1)) * n ** 3, os.path.relpath(f, ROOT)
+    return None, None
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -295,10 +322,13 @@ def roofline_entry(prof, precision, n, peaks, clocks):
     else:
         peak = FP64_PEAK_TFLOPS
         peak_src = "B300 FP64 1.25 TFLOP/s (recipe figure; a DFMA loop measured 0.95 on this pool)"
-    traffic = None  # ncu dram bytes per launch, see profiles/ (null until recaptured for this kernel)
+    traffic, traffic_src = profiled_traffic(dom, n) if precision == 1 else (None, None)
     return {
         "bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-        "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
+        "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_source": traffic_src,
+        "traffic_algorithmic": (n ** 3 * (2 * 5 * 10 * 4 / 2 + 10 * 6 * 4)) if dom == "k_face" else
+        (n ** 3 * (5 * 10 * (4 + 4 + 8 + 8) + 6 * 60 * 4 / 2)),
+        "peak_source": peak_src,
         "algorithmic_flops": f"value-numbered op count per point x points per launch ({oc['face_point']['total_flops']} "
                              f"per face point, {oc['cell_point']['total_flops']} per cell point)",
         "kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}

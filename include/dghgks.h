@@ -75,8 +75,8 @@ typedef struct {
   double tau_eps;
 } dghgks_opts;
 
-/* Create a solver for P_order elements (order 1, 2 or 3; n_q in {order, order+1},
- * n_q >= 2) on `mesh`, for a gas with ratio of specific heats gamma, viscosity
+/* Create a solver for P_order elements (order 1 with n_q = 2; order 2 with
+ * n_q = 2 or 3; order 3 with n_q = 3 or 4) on `mesh`, for a gas with ratio of specific heats gamma, viscosity
  * mu >= 0 and Prandtl number Pr > 0 (Pr = 1 is the BGK value used by the
  * paper; Pr != 1 adds (1/Pr - 1) times the heat flux of the same distribution
  * to the energy flux, which the paper does not define).  opts may be NULL
@@ -156,8 +156,8 @@ int dghgks_status(dghgks_ctx* ctx, void* stream);
  * Jacobians come from forward-mode dual numbers through the same flux code,
  * the projection and trace operators are transposed exactly.  They allocate
  * adjoint scratch on first use (face cotangents 3 x 2 x 5 N_m doubles per
- * cell, a state-sized buffer, per-CTA partials).  FP32-mixed contexts return
- * DGHGKS_EUNSUP. */
+ * cell, a state-sized buffer, per-CTA partials).  FP32-mixed contexts and
+ * order 3 return DGHGKS_EUNSUP. */
 
 /* (lamQ, dmu) = (dL/dQ, dL/dmu)^T lamL + (dL_t/dQ, dL_t/dmu)^T lamLt at Q for
  * the residual of dghgks_residual with the same dt.  lamQ (device, state

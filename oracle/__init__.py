@@ -169,12 +169,14 @@ def enstrophy_dissipation(pb: Problem, Q: np.ndarray, rho0: float = 1.0) -> floa
 
 IC_ADVECTION = 1
 IC_TGV = 2
+IC_VORTEX = 3
 
 
 def project(pb: Problem, ic: int, par) -> np.ndarray:
     """L2 projection of an initial condition of Sec. 5 onto P_k ((k+3)^3 Gauss points).
 
-    ic=1 (advection): par = (amplitude, t); ic=2 (Taylor-Green): par = (V0, rho0, p0, isothermal).
+    ic=1 (advection): par = (amplitude, t); ic=2 (Taylor-Green): par = (V0, rho0, p0, isothermal);
+    ic=3 (isotropic vortex): par = (eps, t, xc, yc, Lx, Ly).
     """
     Q = np.zeros(pb.shape)
     par = np.ascontiguousarray(par, dtype=np.float64)

@@ -894,9 +894,28 @@ inline double enstrophy_dissipation(const Grid& G, const double* Q, double mu, d
 // ic 1: density advection rho = 1 + A sin(pi (x+y+z - 3t)), U=V=W=1, p=1
 //       (par[0] = A, t = par[1]).
 // ic 2: Taylor-Green vortex (par = V0, rho0, p0, isothermal flag).
+// ic 3: isotropic vortex of Sec. 5.1 on [0, Lx] x [0, Ly] (x-y plane, W = 0):
+//       mean flow (rho, U, V, p) = (1, 1, 1, 1) plus the vortex of strength
+//       eps centred at (xc, yc) + t (1, 1) (periodic images), with
+//       dU = eps/(2 pi) e^{(1-r^2)/2} (-y), dV = eps/(2 pi) e^{(1-r^2)/2} x,
+//       dT = -(gamma-1) eps^2/(8 gamma pi^2) e^{1-r^2}, entropy p/rho^gamma = 1
+//       (par = eps, t, xc, yc, Lx, Ly).
 inline void ic_point(int ic, const double* par, const double x[3], double q[5], double gamma) {
   double rho, U, V, W, p;
-  if (ic == 1) {
+  if (ic == 3) {
+    const double eps = par[0], t = par[1], Lx = par[4], Ly = par[5];
+    double dx = x[0] - (par[2] + t), dy = x[1] - (par[3] + t);
+    dx -= Lx * std::floor(dx / Lx + 0.5);  // nearest periodic image
+    dy -= Ly * std::floor(dy / Ly + 0.5);
+    const double r2 = dx * dx + dy * dy;
+    const double f = eps / (2.0 * kPi) * std::exp(0.5 * (1.0 - r2));
+    U = 1.0 - f * dy;
+    V = 1.0 + f * dx;
+    W = 0.0;
+    const double T = 1.0 - (gamma - 1.0) * eps * eps / (8.0 * gamma * kPi * kPi) * std::exp(1.0 - r2);
+    rho = std::pow(T, 1.0 / (gamma - 1.0));
+    p = rho * T;
+  } else if (ic == 1) {
     double t = par[1];
     rho = 1.0 + par[0] * std::sin(kPi * (x[0] + x[1] + x[2] - 3.0 * t));
     U = V = W = 1.0;

@@ -196,14 +196,14 @@ int orc_enstrophy_dissipation(const orc_cfg* c, const double* Q, double rho0, do
 
 int orc_project(const orc_cfg* c, int ic, const double* par, double* Q) {
   orc::Grid G;
-  if (!make_grid(c, G) || (ic != 1 && ic != 2)) return -1;
+  if (!make_grid(c, G) || ic < 1 || ic > 3) return -1;
   orc::project_ic(G, ic, par, c->gamma, Q);
   return 0;
 }
 
 int orc_density_errors(const orc_cfg* c, const double* Q, int ic, const double* par, double* out) {
   orc::Grid G;
-  if (!make_grid(c, G) || (ic != 1 && ic != 2)) return -1;
+  if (!make_grid(c, G) || ic < 1 || ic > 3) return -1;
   orc::density_errors(G, Q, ic, par, c->gamma, out);
   return 0;
 }

@@ -322,6 +322,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
                const size_t mu_offset) {
   using LY = CellLayout<ORDER, NQ>;
   using S = CellAdjSmem<ORDER, NQ>;
+  static_assert(LY::GW == 1, "the adjoint cell kernel handles up to 3^3 points per cell");
   constexpr int NM = LY::NM, NP = LY::NP, NC = S::NC, CB = LY::CB, PG = LY::PG, NOP2 = S::NOP2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double(*cq)[CB] = reinterpret_cast<double(*)[CB]>(smem_raw);

@@ -88,12 +88,16 @@ constexpr int FB = 32;  // faces per CTA in k_face
 // four sub-partitions (16384 registers each) and a CTA's warps are spread
 // over them, so the cap for C resident CTAs of W warps is
 // 16384 / (ceil(C W / 4) x 32), rounded down to a multiple of 8.
-// FP32: 2 CTAs of 9 warps (n_q = 3; 96 registers, a few spills) or 4 CTAs of
-// 4 warps (n_q = 2; 128 registers).  FP64 (bound by the FP64 pipe): 1 CTA.
+// FP32: 2 CTAs of 9 warps (n_q = 3; 96 registers, a few spills), 4 CTAs of
+// 4 warps (n_q = 2; 128 registers) or 1 CTA of 16 warps (n_q = 4; 128).
+// FP64 (bound by the FP64 pipe): 1 CTA.
+#ifndef FACE_CTAS_NQ3
+#define FACE_CTAS_NQ3 2
+#endif
 template <class R, int NQ>
 constexpr int face_max_regs() {
   constexpr int warps = (FB * NQ * NQ + 31) / 32;
-  constexpr int ctas = sizeof(R) == 4 ? (NQ >= 3 ? 2 : 4) : 1;
+  constexpr int ctas = sizeof(R) == 4 ? (NQ == 2 ? 4 : NQ == 3 ? FACE_CTAS_NQ3 : 1) : 1;
   constexpr int per_part = (warps * ctas + 3) / 4;
   constexpr int cap = 16384 / (per_part * 32) / 8 * 8;
   return cap > 255 ? 255 : cap;
@@ -260,20 +264,22 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
 // ---------------------------------------------------------------------------
 enum { MODE_RESIDUAL = 0, MODE_STAGE1 = 1, MODE_STAGE2 = 2 };
 
-// Thread layout of k_cell: a group of PG lanes owns one cell, one lane per
-// Gauss point (NQ^3 <= PG; the spare lanes carry zeros).  8 warps per CTA.
+// Thread layout of k_cell: the NQ^3 Gauss points of a cell are spread over
+// GW warps (GW = 1 for NQ <= 3, 2 for NQ = 4), one lane per point; at
+// NQ <= 3 a group of PG lanes holds one cell (PG = 8 at NQ = 2: four cells
+// per warp).  Spare lanes carry zeros.  8 warps per CTA.
 template <int ORDER, int NQ>
 struct CellLayout {
   static constexpr int NP = NQ * NQ * NQ;
-  static constexpr int PG = NP <= 8 ? 8 : 32;
-  static constexpr int CPW = 32 / PG;
+  static constexpr int GW = (NP + 31) / 32;          // warps per cell
+  static constexpr int PG = NP <= 8 ? 8 : 32;        // lanes of a reduction group
+  static constexpr int CPW = GW == 1 ? 32 / PG : 1;  // cells per warp
   static constexpr int WARPS = 8;
-  static constexpr int CB = CPW * WARPS;  // cells per CTA
+  static constexpr int CB = GW == 1 ? CPW * WARPS : WARPS / GW;  // cells per CTA
   static constexpr int NM = n_modes(ORDER);
   static constexpr int NOUT = 5 * (NM - 1);                 // volume outputs (mode 0 has no gradient)
   static constexpr int NOP = (NOUT + PG - 1) / PG * PG;      // padded to the group width
-  static constexpr int RPL = NOP / PG;                       // reduced outputs per lane
-  static_assert(NP <= 32, "k_cell handles up to 3^3 points per cell");
+  static_assert(NP <= 64, "k_cell handles up to 4^3 points per cell");
 };
 
 template <class R, int ORDER, int NQ>
@@ -281,7 +287,7 @@ struct CellSmem {
   using LY = CellLayout<ORDER, NQ>;
   static constexpr int NM = LY::NM, NC = 5 * NM, CB = LY::CB;
   static constexpr size_t coef = sizeof(R) * NC * CB;
-  static constexpr size_t red = sizeof(R) * CB * 2 * LY::NOP;
+  static constexpr size_t red = sizeof(R) * CB * LY::GW * 2 * LY::NOP;
   static constexpr size_t tabs = sizeof(double) * NM + sizeof(int) * 6 * NM;
   static constexpr size_t bytes = coef + red + tabs;
 };
@@ -338,17 +344,19 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
            const MeshDev m, const double dt, unsigned* __restrict__ flag) {
   using LY = CellLayout<ORDER, NQ>;
   using S = CellSmem<R, ORDER, NQ>;
-  constexpr int NM = LY::NM, NP = LY::NP, NC = S::NC, CB = LY::CB, PG = LY::PG, NT = n_tmodes(ORDER);
-  constexpr int NOUT = LY::NOUT, NOP = LY::NOP, RPL = LY::RPL;
+  constexpr int NM = LY::NM, NP = LY::NP, NC = S::NC, CB = LY::CB, PG = LY::PG, GW = LY::GW, NT = n_tmodes(ORDER);
+  constexpr int NOUT = LY::NOUT, NOP = LY::NOP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R(*coef)[CB] = reinterpret_cast<R(*)[CB]>(smem_raw);
-  R(*red)[2][NOP] = reinterpret_cast<R(*)[2][NOP]>(smem_raw + S::coef);
+  R(*red)[GW][2][NOP] = reinterpret_cast<R(*)[GW][2][NOP]>(smem_raw + S::coef);
   double* invM = reinterpret_cast<double*>(smem_raw + S::coef + S::red);
   int* tix = reinterpret_cast<int*>(invM + NM);  // [3][NM] tangential index, then [3][NM] parity sign
 
   const int tid = threadIdx.x, nthr = LY::WARPS * 32;
-  const int lane = tid & 31, lg = lane % PG;
-  const int cb = (tid >> 5) * LY::CPW + lane / PG;  // cell of this lane within the CTA
+  const int lane = tid & 31, lg = lane % PG, warp = tid >> 5;
+  const int cb = GW == 1 ? warp * LY::CPW + lane / PG : warp / GW;  // cell of this lane within the CTA
+  const int gw = GW == 1 ? 0 : warp % GW;                            // which warp of the cell
+  const int pidx = gw * 32 + lg;                                      // Gauss point of this lane
   const int i0 = blockIdx.x * CB, j = blockIdx.y, k = blockIdx.z;
   const int nx = m.nx, ny = m.ny, nz = m.nz;
   const long long nc = m.ncell;
@@ -369,8 +377,8 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
   __syncthreads();
 
   // ---- interior flux of Eq. (flux-2) at this lane's Gauss point ----
-  const bool active = (lg < NP) && (i0 + cb < nx);
-  const int pp = active ? lg : 0;
+  const bool active = (pidx < NP) && (i0 + cb < nx);
+  const int pp = active ? pidx : 0;
   const int pa[3] = {pp / (NQ * NQ), (pp / NQ) % NQ, pp % NQ};
   R L1[3][ORDER + 1], dL1[3][ORDER + 1];
 #pragma unroll
@@ -417,27 +425,31 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
       }
   }
 
-  // ---- volume projection: sum over the group's points of Fw . grad B_n (n >= 1) ----
+  // ---- volume projection: sum over the group's points of Fw . grad B_n (n >= 1),
+  // PG outputs at a time (lane lg ends with output c0 + lg of each chunk) ----
 #pragma unroll
   for (int kind = 0; kind < 2; ++kind) {
-    R val[NOP];
 #pragma unroll
-    for (int o = 0; o < NOP; ++o) {
-      R c = R(0);
-      if (o < NOUT) {
-        const int v = o / (NM - 1), n = 1 + o % (NM - 1);
-        const int e0 = mode_exp(n, 0), e1 = mode_exp(n, 1), e2 = mode_exp(n, 2);
-        const R(&Fk)[3][5] = kind == 0 ? Fw : Ftw;
-        if (e0 > 0) c += Fk[0][v] * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
-        if (e1 > 0) c += Fk[1][v] * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
-        if (e2 > 0) c += Fk[2][v] * (L1[0][e0] * L1[1][e1] * dL1[2][e2]);
+    for (int c0 = 0; c0 < NOP; c0 += PG) {
+      R val[PG];
+#pragma unroll
+      for (int oo = 0; oo < PG; ++oo) {
+        const int o = c0 + oo;
+        R c = R(0);
+        if (o < NOUT) {
+          const int v = o / (NM - 1), n = 1 + o % (NM - 1);
+          const int e0 = mode_exp(n, 0), e1 = mode_exp(n, 1), e2 = mode_exp(n, 2);
+          const R(&Fk)[3][5] = kind == 0 ? Fw : Ftw;
+          if (e0 > 0) c += Fk[0][v] * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
+          if (e1 > 0) c += Fk[1][v] * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
+          if (e2 > 0) c += Fk[2][v] * (L1[0][e0] * L1[1][e1] * dL1[2][e2]);
+        }
+        val[oo] = c;
       }
-      val[o] = c;
+      R outv[1];
+      group_reduce<PG, PG>(val, outv, lg);
+      red[cb][gw][kind][c0 + lg] = outv[0];
     }
-    R outv[RPL];
-    group_reduce<NOP, PG>(val, outv, lg);
-#pragma unroll
-    for (int r = 0; r < RPL; ++r) red[cb][kind][RPL * lg + r] = outv[r];
   }
   __syncthreads();
 
@@ -448,8 +460,13 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
     if (i >= nx) continue;
     const size_t cell = row + i;
     const size_t idx = (size_t)(v * NM + mm) * nc + cell;
-    R sF = mm == 0 ? R(0) : red[cc][0][v * (NM - 1) + mm - 1];
-    R sT = mm == 0 ? R(0) : red[cc][1][v * (NM - 1) + mm - 1];
+    R sF = R(0), sT = R(0);
+    if (mm > 0)
+#pragma unroll
+      for (int g = 0; g < GW; ++g) {
+        sF += red[cc][g][0][v * (NM - 1) + mm - 1];
+        sT += red[cc][g][1][v * (NM - 1) + mm - 1];
+      }
 #pragma unroll
     for (int D = 0; D < 3; ++D) {
       const int t = tix[D * NM + mm];

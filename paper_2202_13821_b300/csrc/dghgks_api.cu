@@ -239,12 +239,18 @@ const Ops kOps64_2_3 = DG_OPS(double, 2, 3);
 const Ops kOps32_1_2 = DG_OPS(float, 1, 2);
 const Ops kOps32_2_2 = DG_OPS(float, 2, 2);
 const Ops kOps32_2_3 = DG_OPS(float, 2, 3);
+const Ops kOps64_3_3 = DG_OPS(double, 3, 3);
+const Ops kOps64_3_4 = DG_OPS(double, 3, 4);
+const Ops kOps32_3_3 = DG_OPS(float, 3, 3);
+const Ops kOps32_3_4 = DG_OPS(float, 3, 4);
 
 const Ops* select_ops(int precision, int order, int nq) {
   const bool f64 = precision == DGHGKS_FP64;
   if (order == 1 && nq == 2) return f64 ? &kOps64_1_2 : &kOps32_1_2;
   if (order == 2 && nq == 2) return f64 ? &kOps64_2_2 : &kOps32_2_2;
   if (order == 2 && nq == 3) return f64 ? &kOps64_2_3 : &kOps32_2_3;
+  if (order == 3 && nq == 3) return f64 ? &kOps64_3_3 : &kOps32_3_3;
+  if (order == 3 && nq == 4) return f64 ? &kOps64_3_4 : &kOps32_3_4;
   return nullptr;
 }
 
@@ -609,6 +615,7 @@ int dghgks_profile_read(dghgks_ctx* c, double* ms, int64_t* launches) {
 
 static int adj_prepare(dghgks_ctx* c) {
   if (c->precision != DGHGKS_FP64) return fail(c, DGHGKS_EUNSUP, "the adjoint needs an FP64 context");
+  if (c->order > 2) return fail(c, DGHGKS_EUNSUP, "the adjoint supports orders 1 and 2");
   if (c->adjH) return DGHGKS_OK;
   const size_t nc = (size_t)c->ncell;
   const size_t state = sizeof(double) * 5 * (size_t)c->nm * nc;
@@ -691,6 +698,7 @@ int dghgks_adjoint_step(dghgks_ctx* c, const double* Qn, const double* lam_next,
 
 int dghgks_kinetic_energy_vjp(dghgks_ctx* c, const double* Q, double rho0, double* dEk_dQ, void* stream) {
   if (!c) return DGHGKS_EARG;
+  if (c->order > 2) return fail(c, DGHGKS_EUNSUP, "the adjoint supports orders 1 and 2");
   if (!Q || !dEk_dQ || dEk_dQ == Q) return fail(c, DGHGKS_EARG, "bad argument");
   if (!(rho0 > 0)) return fail(c, DGHGKS_EARG, "rho0 must be > 0");
   const double omega = c->vol * (double)c->ncell;

@@ -119,7 +119,25 @@ def test_random_discontinuous_states(torch, api, orc, order, nq, mu, tau_eps, Pr
     assert_residual_parity(L, Lt, ref)
 
 
-@pytest.mark.parametrize("order,nq,case", [(1, 2, "adv"), (2, 3, "tgv")])
+@pytest.mark.parametrize("nq", [3, 4])
+@pytest.mark.parametrize("state", ["tgv", "random"])
+def test_p3_residual(torch, api, orc, nq, state):
+    """P3 elements (20 modes), the paper's fourth-order case, with n_q = 3 (the paper's rule) and 4."""
+    from paper_2202_13821_b300 import inputs
+
+    if state == "tgv":
+        n = (9, 5, 6)
+        s, pb = make(api, orc, n, order=3, nq=nq, mu=1 / 1600, Pr=0.72, **TGV)
+        Q = inputs.modal_state(inputs.tgv_prim, n, 3, TGV["lo"], TGV["hi"], perturb=1e-3)
+    else:
+        n = (5, 3, 4)
+        s, pb = make(api, orc, n, lo=(0, 0, 0), hi=(1.0, 0.8, 0.6), order=3, nq=nq, mu=3e-3, tau_eps=0.02)
+        Q = inputs.random_state(n, 3, seed=5)
+    L, Lt, ref = residual_pair(torch, s, pb, orc, Q, 1.5e-3)
+    assert_residual_parity(L, Lt, ref)
+
+
+@pytest.mark.parametrize("order,nq,case", [(1, 2, "adv"), (2, 3, "tgv"), (3, 4, "tgv")])
 def test_s2o4_step_parity(torch, api, orc, order, nq, case):
     from paper_2202_13821_b300 import inputs
 

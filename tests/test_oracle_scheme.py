@@ -84,6 +84,26 @@ def test_advection_convergence_order(orc, order, n0, min_order):
     assert bad[1] > 20 * e1[1]
 
 
+def vortex_errors(orc, order, n, T=1.0, cfl=0.1):
+    """Isotropic vortex of Sec. 5.1 as a 3-D problem with one cell along z; errors at time T.
+    The vortex centre is the centre (5, 5) of the [0, 10]^2 domain (the paper's r is measured
+    from it); the exact solution is the initial vortex moved by T (1, 1)."""
+    h = 10.0 / n
+    dt0 = cfl * h / (math.sqrt(2) + 1.0 + math.sqrt(1.4))
+    ns = math.ceil(T / dt0)
+    pb = orc.Problem(order=order, nq=order + 1, n=(n, n, 1), lo=(0.0, 0.0, 0.0), hi=(10.0, 10.0, h))
+    Q = orc.project(pb, orc.IC_VORTEX, (5.0, 0.0, 5.0, 5.0, 10.0, 10.0))
+    Q = orc.step(pb, Q, T / ns, ns)
+    return orc.density_errors(pb, Q, orc.IC_VORTEX, (5.0, T, 5.0, 5.0, 10.0, 10.0))
+
+
+@pytest.mark.slow
+def test_isotropic_vortex_p1_order(orc):
+    e0, e1 = vortex_errors(orc, 1, 20), vortex_errors(orc, 1, 40)
+    orders = np.log2(e0 / e1)
+    assert orders[1] > 1.7, orders  # L2 order ~ k+1 = 2
+
+
 def test_golden_orders_fixture_is_k_plus_1():
     rows = [l.split() for l in open(os.path.join(HERE, "golden", "advection_orders.txt")) if l[0] != "#"]
     for k, expect, finest in rows:
