@@ -42,7 +42,7 @@ N_CELLS_1D = 256
 ORDER, NQ = 2, 3
 MU, PR, GAMMA, MA = 1.0 / 1600.0, 0.72, 1.4, 0.1
 FP32_PEAK_NOTE = "148 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"
-FP64_PEAK_TFLOPS = 1.25  # B300 FP64 figure of the pool's profiling recipe
+FP64_PEAK_TFLOPS = 1.25  # B300 nominal FP64 (non-tensor) rate
 
 
 def parse():
@@ -321,7 +321,7 @@ def roofline_entry(prof, precision, n, peaks, clocks):
         peak_src = f"derived: {FP32_PEAK_NOTE} = {peak:.1f} TFLOP/s (FP32)"
     else:
         peak = FP64_PEAK_TFLOPS
-        peak_src = "B300 FP64 1.25 TFLOP/s (recipe figure; a DFMA loop measured 0.95 on this pool)"
+        peak_src = "B300 FP64 1.25 TFLOP/s nominal (a DFMA loop measured 0.95 on a B300)"
     traffic, traffic_src = profiled_traffic(dom, n) if precision == 1 else (None, None)
     return {
         "bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",

@@ -57,13 +57,22 @@ extern "C" {
 
 typedef struct dghgks_ctx dghgks_ctx;
 
-/* Uniform Cartesian hexahedral mesh K_ijk = [x_{i-1/2}, x_{i+1/2}] x ... (Sec. 3).
- * nx, ny, nz >= 1 cells on the box [lo, hi]; only periodic boundaries are
- * supported (periodic[d] must be 1). */
+/* Cartesian hexahedral mesh K_ijk = [x_{i-1/2}, x_{i+1/2}] x ... (Sec. 3).
+ * nx, ny, nz >= 1 cells; only periodic boundaries are supported
+ * (periodic[d] must be 1).
+ * nodes[d] == NULL: uniform cells of width (hi[d] - lo[d]) / n_d along axis d.
+ * nodes[d] != NULL: host array of the n_d + 1 strictly increasing node
+ * coordinates x_{1/2} .. x_{n_d+1/2} of axis d (a rectilinear, non-uniform
+ * mesh such as the mapped grid x = xi + 0.05 sin(pi xi) of Sec. 5.1);
+ * lo[d] and hi[d] are then ignored.  dghgks_init copies the nodes (the
+ * caller keeps ownership); non-increasing or non-finite nodes give
+ * DGHGKS_EARG.  Fields must be zero-initialised (NULL nodes) by callers that
+ * want the uniform mesh. */
 typedef struct {
   int nx, ny, nz;
   double lo[3], hi[3];
   int periodic[3];
+  const double* nodes[3];
 } dghgks_mesh;
 
 /* n_q: Gauss points per direction (faces n_q^2, cells n_q^3); 0 = order+1.

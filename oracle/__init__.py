@@ -49,7 +49,7 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("nq", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nz", ctypes.c_int), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
                 ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
-                ("tau_eps", ctypes.c_double)]
+                ("tau_eps", ctypes.c_double), ("nodes", ctypes.POINTER(ctypes.c_double) * 3)]
 
 
 def lib():
@@ -67,7 +67,11 @@ def _p(a: np.ndarray):
 
 @dataclass
 class Problem:
-    """Uniform periodic hexahedral grid and gas parameters (oracle side)."""
+    """Periodic rectilinear hexahedral grid and gas parameters (oracle side).
+
+    ``nodes``: None (uniform cells between lo and hi) or, per axis, None or the
+    n_d + 1 increasing node coordinates of that axis (lo/hi then follow them).
+    """
     order: int = 1
     nq: int = 2
     n: tuple = (8, 8, 8)
@@ -77,6 +81,7 @@ class Problem:
     mu: float = 0.0
     Pr: float = 1.0
     tau_eps: float = 0.0
+    nodes: tuple = None
 
     def cfg(self) -> _Cfg:
         c = _Cfg()
@@ -85,6 +90,15 @@ class Problem:
         for d in range(3):
             c.lo[d], c.hi[d] = self.lo[d], self.hi[d]
         c.gamma, c.mu, c.Pr, c.tau_eps = self.gamma, self.mu, self.Pr, self.tau_eps
+        c._keep = []
+        for d in range(3):
+            nd = None if self.nodes is None else self.nodes[d]
+            if nd is not None:
+                a = np.ascontiguousarray(nd, dtype=np.float64)
+                if a.shape != (self.n[d] + 1,):
+                    raise ValueError(f"axis {d}: {self.n[d] + 1} nodes expected, got {a.shape}")
+                c._keep.append(a)
+                c.nodes[d] = _p(a)
         return c
 
     @property
@@ -170,6 +184,7 @@ def enstrophy_dissipation(pb: Problem, Q: np.ndarray, rho0: float = 1.0) -> floa
 IC_ADVECTION = 1
 IC_TGV = 2
 IC_VORTEX = 3
+IC_SHEAR = 4  # par = (eps, axis d, lo_d, span_d, rho, p): u_{(d+1)%3} = eps sin(2 pi (x_d - lo_d)/span_d)
 
 
 def project(pb: Problem, ic: int, par) -> np.ndarray:

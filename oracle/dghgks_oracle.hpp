@@ -654,7 +654,14 @@ struct Grid {
   int order = 1, nq = 2;
   int n[3] = {1, 1, 1};
   double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  // optional node coordinates per axis (n[d] + 1 increasing values); empty = uniform
+  std::vector<double> nodes[3];
   double h(int d) const { return (hi[d] - lo[d]) / n[d]; }
+  // width of cell c along axis d
+  double hc(int d, int c) const { return nodes[d].empty() ? h(d) : nodes[d][c + 1] - nodes[d][c]; }
+  // left node of cell c along axis d
+  double x0(int d, int c) const { return nodes[d].empty() ? lo[d] + c * h(d) : nodes[d][c]; }
+  double vol(int i, int j, int k) const { return hc(0, i) * hc(1, j) * hc(2, k); }
   int64_t cells() const { return (int64_t)n[0] * n[1] * n[2]; }
   int nm() const { return n_modes(order); }
   // state layout Q[var][mode][z][y][x]
@@ -673,8 +680,9 @@ inline void trace(const Grid& G, const std::vector<Mode>& md, const T* Q, int i,
   }
   for (int m = 0; m < (int)md.size(); ++m) {
     double b = basis(md[m], r);
+    const int c3[3] = {i, j, k};
     double db[3];
-    for (int d = 0; d < 3; ++d) db[d] = dbasis(md[m], r, d) * 2.0 / G.h(d);
+    for (int d = 0; d < 3; ++d) db[d] = dbasis(md[m], r, d) * 2.0 / G.hc(d, c3[d]);
     for (int v = 0; v < 5; ++v) {
       T c = Q[G.idx(v, m, i, j, k)];
       q[v] += c * b;
@@ -698,7 +706,7 @@ inline bool residual_cell(const Grid& G, const Phys<T>& ph, const T* Q, double d
   const int nm = (int)md.size(), nq = G.nq;
   double gx[8], gw[8];
   gauss_rule(nq, gx, gw);
-  const double vol = G.h(0) * G.h(1) * G.h(2);
+  const double vol = G.vol(i, j, k);
   std::vector<T> R(5 * nm, T(0.0)), Rt(5 * nm, T(0.0));
   std::vector<double> Ra(5 * nm, 0.0), Rta(5 * nm, 0.0);
 
@@ -713,7 +721,8 @@ inline bool residual_cell(const Grid& G, const Phys<T>& ph, const T* Q, double d
         if (!cell_flux(q, dq, ph, dt, F, Ft)) return false;
         for (int m = 0; m < nm; ++m) {
           double gb[3];
-          for (int d = 0; d < 3; ++d) gb[d] = dbasis(md[m], r, d) * 2.0 / G.h(d);
+          const int c3[3] = {i, j, k};
+          for (int d = 0; d < 3; ++d) gb[d] = dbasis(md[m], r, d) * 2.0 / G.hc(d, c3[d]);
           for (int v = 0; v < 5; ++v)
             for (int d = 0; d < 3; ++d) {
               R[v * nm + m] += w * F[d][v] * gb[d];
@@ -728,7 +737,7 @@ inline bool residual_cell(const Grid& G, const Phys<T>& ph, const T* Q, double d
   const int c0[3] = {i, j, k};
   for (int d = 0; d < 3; ++d) {
     int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;  // tangential axes, increasing
-    double area = vol / G.h(d);
+    double area = vol / G.hc(d, c0[d]);  // the same for both cells of the face
     for (int s = -1; s <= 1; s += 2) {
       int nb[3] = {c0[0], c0[1], c0[2]};
       nb[d] = wrap(c0[d] + s, G.n[d]);
@@ -828,13 +837,12 @@ inline bool s2o4_step(const Grid& G, const Phys<T>& ph, T* Q, double dt) {
 // conserved totals: int_Omega Q_h = sum_cells |K| Q_{v, mode 0}
 template <class T>
 inline void totals(const Grid& G, const T* Q, T out[5]) {
-  const double vol = G.h(0) * G.h(1) * G.h(2);
   for (int v = 0; v < 5; ++v) {
     T s = T(0.0);
     for (int k = 0; k < G.n[2]; ++k)
       for (int j = 0; j < G.n[1]; ++j)
-        for (int i = 0; i < G.n[0]; ++i) s += Q[G.idx(v, 0, i, j, k)];
-    out[v] = s * vol;
+        for (int i = 0; i < G.n[0]; ++i) s += G.vol(i, j, k) * Q[G.idx(v, 0, i, j, k)];
+    out[v] = s;
   }
 }
 
@@ -844,7 +852,7 @@ inline T kinetic_energy(const Grid& G, const T* Q, double rho0) {
   const std::vector<Mode> md = mode_list(G.order);
   double gx[8], gw[8];
   gauss_rule(G.nq, gx, gw);
-  const double vol = G.h(0) * G.h(1) * G.h(2);
+  double omega = 0.0;
   T s = T(0.0);
   for (int k = 0; k < G.n[2]; ++k)
     for (int j = 0; j < G.n[1]; ++j)
@@ -852,6 +860,8 @@ inline T kinetic_energy(const Grid& G, const T* Q, double rho0) {
         for (int a = 0; a < G.nq; ++a)
           for (int b = 0; b < G.nq; ++b)
             for (int c = 0; c < G.nq; ++c) {
+              const double vol = G.vol(i, j, k);
+              if (a == 0 && b == 0 && c == 0) omega += vol;
               double r[3] = {gx[a], gx[b], gx[c]};
               T q[5];
               for (int v = 0; v < 5; ++v) {
@@ -860,7 +870,7 @@ inline T kinetic_energy(const Grid& G, const T* Q, double rho0) {
               }
               s += gw[a] * gw[b] * gw[c] * vol * 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0];
             }
-  return s / (rho0 * vol * G.cells());
+  return s / (rho0 * omega);
 }
 
 // Enstrophy-based dissipation of Sec. 5.3:
@@ -869,14 +879,15 @@ inline double enstrophy_dissipation(const Grid& G, const double* Q, double mu, d
   const std::vector<Mode> md = mode_list(G.order);
   double gx[8], gw[8];
   gauss_rule(G.nq, gx, gw);
-  const double vol = G.h(0) * G.h(1) * G.h(2);
-  double s = 0.0;
+  double s = 0.0, omega = 0.0;
   for (int k = 0; k < G.n[2]; ++k)
     for (int j = 0; j < G.n[1]; ++j)
       for (int i = 0; i < G.n[0]; ++i)
         for (int a = 0; a < G.nq; ++a)
           for (int b = 0; b < G.nq; ++b)
             for (int c = 0; c < G.nq; ++c) {
+              const double vol = G.vol(i, j, k);
+              if (a == 0 && b == 0 && c == 0) omega += vol;
               const double r[3] = {gx[a], gx[b], gx[c]};
               double q[5], dq[3][5];
               trace(G, md, Q, i, j, k, r, q, dq);
@@ -887,7 +898,7 @@ inline double enstrophy_dissipation(const Grid& G, const double* Q, double mu, d
               const double w[3] = {du[1][2] - du[2][1], du[2][0] - du[0][2], du[0][1] - du[1][0]};
               s += gw[a] * gw[b] * gw[c] * vol * 0.5 * q[0] * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
             }
-  return 2.0 * mu * s / (rho0 * vol * G.cells());
+  return 2.0 * mu * s / (rho0 * omega);
 }
 
 // Initial conditions of Sec. 5 as conservative variables at a point.
@@ -902,7 +913,19 @@ inline double enstrophy_dissipation(const Grid& G, const double* Q, double mu, d
 //       (par = eps, t, xc, yc, Lx, Ly).
 inline void ic_point(int ic, const double* par, const double x[3], double q[5], double gamma) {
   double rho, U, V, W, p;
-  if (ic == 3) {
+  if (ic == 4) {
+    // transverse shear wave: velocity component (d+1) mod 3 equal to
+    // eps sin(2 pi (x_d - lo_d) / span_d), uniform density and pressure;
+    // par = (eps, d, lo_d, span_d, rho, p)
+    const int d = (int)par[1];
+    double vel[3] = {0.0, 0.0, 0.0};
+    vel[(d + 1) % 3] = par[0] * std::sin(2.0 * kPi * (x[d] - par[2]) / par[3]);
+    U = vel[0];
+    V = vel[1];
+    W = vel[2];
+    rho = par[4];
+    p = par[5];
+  } else if (ic == 3) {
     const double eps = par[0], t = par[1], Lx = par[4], Ly = par[5];
     double dx = x[0] - (par[2] + t), dy = x[1] - (par[3] + t);
     dx -= Lx * std::floor(dx / Lx + 0.5);  // nearest periodic image
@@ -941,18 +964,18 @@ inline void project_ic(const Grid& G, int ic, const double* par, double gamma, d
   const int nm = (int)md.size(), nq = G.order + 3;
   double gx[8], gw[8];
   gauss_rule(nq, gx, gw);
-  const double vol = G.h(0) * G.h(1) * G.h(2);
 #pragma omp parallel for collapse(2)
   for (int k = 0; k < G.n[2]; ++k)
     for (int j = 0; j < G.n[1]; ++j)
       for (int i = 0; i < G.n[0]; ++i) {
         std::vector<double> acc(5 * nm, 0.0);
+        const double vol = G.vol(i, j, k);
         for (int a = 0; a < nq; ++a)
           for (int b = 0; b < nq; ++b)
             for (int c = 0; c < nq; ++c) {
               double r[3] = {gx[a], gx[b], gx[c]};
-              double x[3] = {G.lo[0] + (i + 0.5 * (1 + r[0])) * G.h(0), G.lo[1] + (j + 0.5 * (1 + r[1])) * G.h(1),
-                             G.lo[2] + (k + 0.5 * (1 + r[2])) * G.h(2)};
+              double x[3] = {G.x0(0, i) + 0.5 * (1 + r[0]) * G.hc(0, i), G.x0(1, j) + 0.5 * (1 + r[1]) * G.hc(1, j),
+                             G.x0(2, k) + 0.5 * (1 + r[2]) * G.hc(2, k)};
               double q[5];
               ic_point(ic, par, x, q, gamma);
               double w = gw[a] * gw[b] * gw[c] * vol;
@@ -973,18 +996,18 @@ inline void density_errors(const Grid& G, const double* Q, int ic, const double*
   const int nq = G.order + 3;
   double gx[8], gw[8];
   gauss_rule(nq, gx, gw);
-  const double vol = G.h(0) * G.h(1) * G.h(2);
   double e1 = 0, e2 = 0, ec = 0;
   for (int k = 0; k < G.n[2]; ++k)
     for (int j = 0; j < G.n[1]; ++j)
       for (int i = 0; i < G.n[0]; ++i) {
         double avg_exact = 0;
+        const double vol = G.vol(i, j, k);
         for (int a = 0; a < nq; ++a)
           for (int b = 0; b < nq; ++b)
             for (int c = 0; c < nq; ++c) {
               double r[3] = {gx[a], gx[b], gx[c]};
-              double x[3] = {G.lo[0] + (i + 0.5 * (1 + r[0])) * G.h(0), G.lo[1] + (j + 0.5 * (1 + r[1])) * G.h(1),
-                             G.lo[2] + (k + 0.5 * (1 + r[2])) * G.h(2)};
+              double x[3] = {G.x0(0, i) + 0.5 * (1 + r[0]) * G.hc(0, i), G.x0(1, j) + 0.5 * (1 + r[1]) * G.hc(1, j),
+                             G.x0(2, k) + 0.5 * (1 + r[2]) * G.hc(2, k)};
               double q[5];
               ic_point(ic, par, x, q, gamma);
               double rh = 0;

@@ -16,6 +16,9 @@ typedef struct {
   int order, nq, nx, ny, nz;
   double lo[3], hi[3];
   double gamma, mu, Pr, tau_eps;
+  // optional node coordinates per axis (n_d + 1 increasing values; NULL = uniform
+  // cells between lo and hi); when given, lo/hi of that axis are taken from them
+  const double* nodes[3];
 } orc_cfg;
 }
 
@@ -30,7 +33,14 @@ static bool make_grid(const orc_cfg* c, orc::Grid& G) {
   for (int d = 0; d < 3; ++d) {
     G.lo[d] = c->lo[d];
     G.hi[d] = c->hi[d];
-    if (!(c->hi[d] > c->lo[d])) return false;
+    if (c->nodes[d]) {
+      G.nodes[d].assign(c->nodes[d], c->nodes[d] + G.n[d] + 1);
+      for (int q = 0; q < G.n[d]; ++q)
+        if (!(G.nodes[d][q + 1] > G.nodes[d][q])) return false;
+      G.lo[d] = G.nodes[d].front();
+      G.hi[d] = G.nodes[d].back();
+    }
+    if (!(G.hi[d] > G.lo[d])) return false;
   }
   return true;
 }
@@ -196,14 +206,14 @@ int orc_enstrophy_dissipation(const orc_cfg* c, const double* Q, double rho0, do
 
 int orc_project(const orc_cfg* c, int ic, const double* par, double* Q) {
   orc::Grid G;
-  if (!make_grid(c, G) || ic < 1 || ic > 3) return -1;
+  if (!make_grid(c, G) || ic < 1 || ic > 4) return -1;
   orc::project_ic(G, ic, par, c->gamma, Q);
   return 0;
 }
 
 int orc_density_errors(const orc_cfg* c, const double* Q, int ic, const double* par, double* out) {
   orc::Grid G;
-  if (!make_grid(c, G) || ic < 1 || ic > 3) return -1;
+  if (!make_grid(c, G) || ic < 1 || ic > 4) return -1;
   orc::density_errors(G, Q, ic, par, c->gamma, out);
   return 0;
 }

@@ -32,7 +32,8 @@ class DghgksError(RuntimeError):
 
 class Mesh(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("lo", ctypes.c_double * 3),
-                ("hi", ctypes.c_double * 3), ("periodic", ctypes.c_int * 3)]
+                ("hi", ctypes.c_double * 3), ("periodic", ctypes.c_int * 3),
+                ("nodes", ctypes.POINTER(ctypes.c_double) * 3)]
 
 
 class Opts(ctypes.Structure):
@@ -117,11 +118,20 @@ def _check(ctx, rc: int):
 # ---- functions with the C names ----
 
 def dghgks_init(n, lo, hi, order: int, gamma: float, mu: float, Pr: float, n_q: int = 0,
-                precision: int = DGHGKS_FP64, tau_eps: float = 0.0):
+                precision: int = DGHGKS_FP64, tau_eps: float = 0.0, nodes=None):
+    """nodes: None, or per axis None / the n_d + 1 increasing node coordinates (host)."""
     m = Mesh()
     m.nx, m.ny, m.nz = (int(v) for v in n)
+    keep = []
     for d in range(3):
         m.lo[d], m.hi[d], m.periodic[d] = lo[d], hi[d], 1
+        nd = None if nodes is None else nodes[d]
+        if nd is not None:
+            a = np.ascontiguousarray(nd, dtype=np.float64)
+            if a.shape != (int(n[d]) + 1,):
+                raise ValueError(f"axis {d}: wrong number of mesh nodes {a.shape}")
+            keep.append(a)
+            m.nodes[d] = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     o = Opts(int(n_q), int(precision), float(tau_eps))
     ctx = _VP()
     rc = load().dghgks_init(ctypes.byref(m), int(order), gamma, mu, Pr, ctypes.byref(o), ctypes.byref(ctx))
@@ -251,11 +261,12 @@ class Solver:
     n_q: int = 0
     precision: int = DGHGKS_FP64
     tau_eps: float = 0.0
+    nodes: tuple = None  # rectilinear mesh: per axis None or n_d + 1 node coordinates
 
     def __post_init__(self):
         self.n = tuple(int(v) for v in self.n)
         self.ctx = dghgks_init(self.n, self.lo, self.hi, self.order, self.gamma, self.mu, self.Pr, self.n_q,
-                               self.precision, self.tau_eps)
+                               self.precision, self.tau_eps, self.nodes)
         self.n_modes = load().dghgks_n_modes(self.ctx)
 
     @property

@@ -54,7 +54,15 @@ struct MeshDev {
   float sc_f[3];    // 2 / h_d
   float area_f[3];  // |Gamma| of a face normal to d
   float vol_f;
+  // Rectilinear (non-uniform) meshes: per axis d, the n_d cell widths followed
+  // by the n_d values 2 / width, in FP64 and FP32.  All null on a uniform mesh,
+  // where the scalars above hold.
+  const double* geo64[3];
+  const float* geo32[3];
 };
+
+__device__ __forceinline__ bool mesh_nonuniform(const MeshDev& m) { return m.geo64[0] != nullptr; }
+__device__ __forceinline__ int mesh_n(const MeshDev& m, int d) { return d == 0 ? m.nx : (d == 1 ? m.ny : m.nz); }
 
 // per-precision access to the mesh scales
 template <class R>
@@ -81,6 +89,36 @@ template <>
 __device__ __forceinline__ float mesh_vol<float>(const MeshDev& m) {
   return m.vol_f;
 }
+template <class R>
+__device__ __forceinline__ const R* mesh_geo(const MeshDev& m, int d) {
+  return reinterpret_cast<const R*>(m.geo64[d]);
+}
+template <>
+__device__ __forceinline__ const float* mesh_geo<float>(const MeshDev& m, int d) {
+  return m.geo32[d];
+}
+// width of cell c along axis d
+template <class R>
+__device__ __forceinline__ R cell_w(const MeshDev& m, int d, int c) {
+  return mesh_nonuniform(m) ? __ldg(mesh_geo<R>(m, d) + c) : (R)m.h[d];
+}
+// 2 / width of cell c along axis d (the reference-to-physical gradient scale)
+template <class R>
+__device__ __forceinline__ R cell_sc(const MeshDev& m, int d, int c) {
+  return mesh_nonuniform(m) ? __ldg(mesh_geo<R>(m, d) + mesh_n(m, d) + c) : mesh_sc<R>(m, d);
+}
+// |Gamma| of the face normal to d whose tangential cells are c1 (axis tan1) and c2 (axis tan2)
+template <class R>
+__device__ __forceinline__ R face_area(const MeshDev& m, int d, int c1, int c2) {
+  return mesh_nonuniform(m) ? cell_w<R>(m, tan1(d), c1) * cell_w<R>(m, tan2(d), c2) : mesh_area<R>(m, d);
+}
+// FP64 volume of cell c (linear index) on a rectilinear mesh; 1 on a uniform
+// mesh, where the reductions scale by the common volume at the end
+__device__ __forceinline__ double cell_weight(const MeshDev& m, long long c) {
+  if (!mesh_nonuniform(m)) return 1.0;
+  const int i = (int)(c % m.nx), j = (int)((c / m.nx) % m.ny), k = (int)(c / ((long long)m.nx * m.ny));
+  return __ldg(m.geo64[0] + i) * __ldg(m.geo64[1] + j) * __ldg(m.geo64[2] + k);
+}
 
 constexpr int FB = 32;  // faces per CTA in k_face
 
@@ -88,11 +126,12 @@ constexpr int FB = 32;  // faces per CTA in k_face
 // four sub-partitions (16384 registers each) and a CTA's warps are spread
 // over them, so the cap for C resident CTAs of W warps is
 // 16384 / (ceil(C W / 4) x 32), rounded down to a multiple of 8.
-// FP32: 2 CTAs of 9 warps (n_q = 3; 96 registers, a few spills), 4 CTAs of
-// 4 warps (n_q = 2; 128 registers) or 1 CTA of 16 warps (n_q = 4; 128).
+// FP32: 3 CTAs of 9 warps (n_q = 3; 72 registers: more spills than 2 CTAs at
+// 96, but the extra warps hide them -- 2-7% faster per direction at 256^3),
+// 4 CTAs of 4 warps (n_q = 2; 128 registers) or 1 CTA of 16 warps (n_q = 4; 128).
 // FP64 (bound by the FP64 pipe): 1 CTA.
 #ifndef FACE_CTAS_NQ3
-#define FACE_CTAS_NQ3 2
+#define FACE_CTAS_NQ3 3
 #endif
 template <class R, int NQ>
 constexpr int face_max_regs() {
@@ -167,7 +206,13 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
     Lb[n] = leg<R>(n, xb);
     dLb[n] = dleg<R>(n, xb);
   }
-  const R sD = mesh_sc<R>(m, D), s1 = mesh_sc<R>(m, T1), s2 = mesh_sc<R>(m, T2);
+  // gradient scales: along D those of the left and right cells, tangential
+  // ones shared by both cells (rectilinear mesh)
+  const int ic = active ? i : 0;
+  const int cidx[3] = {ic, j, k};
+  const int nAx = D == 0 ? nx : (D == 1 ? ny : nz);
+  const R sDs[2] = {cell_sc<R>(m, D, wrapm(cidx[D] - 1, nAx)), cell_sc<R>(m, D, cidx[D])};
+  const R s1 = cell_sc<R>(m, T1, cidx[T1]), s2 = cell_sc<R>(m, T2, cidx[T2]);
 
   // Each side in turn: traces at r_D = +1 of the left cell (side 0) or r_D = -1
   // of the right cell (side 1), rotated to the local frame (axes D, D+1, D+2
@@ -197,7 +242,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
         g2 += c * (pn * La[n1] * dLb[n2]);
       }
       q[v] = s0;
-      dq[D][v] = gD * sD;
+      dq[D][v] = gD * sDs[side];
       dq[T1][v] = g1 * s1;
       dq[T2][v] = g2 * s2;
     }
@@ -225,7 +270,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   R Fl[5], Ftl[5];
   ok = iface_finish(sums, gp, Fl, Ftl) && ok;
   if (active && !ok) atomicOr(flag, 1u);
-  const R w = active ? gauss_wr<R>(NQ, a) * gauss_wr<R>(NQ, b) * mesh_area<R>(m, D) : R(0);
+  const R w = active ? gauss_wr<R>(NQ, a) * gauss_wr<R>(NQ, b) * face_area<R>(m, D, cidx[T1], cidx[T2]) : R(0);
   Fs[0][p][f] = w * Fl[0];
   Fs[1 + A0][p][f] = w * Fl[1];
   Fs[1 + A1][p][f] = w * Fl[2];
@@ -367,7 +412,10 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
     coef[comp][cc] = (i < nx) ? (R)__ldg(Qin + (size_t)comp * nc + row + i) : R(0);
   }
   for (int e = tid; e < NM; e += nthr) {
-    invM[e] = (double)((2 * mode_exp(e, 0) + 1) * (2 * mode_exp(e, 1) + 1) * (2 * mode_exp(e, 2) + 1)) / m.vol;
+    // (2a+1)(2b+1)(2c+1) / |K|; on a rectilinear mesh the 1/|K| of each cell
+    // is applied in the epilogue
+    invM[e] = (double)((2 * mode_exp(e, 0) + 1) * (2 * mode_exp(e, 1) + 1) * (2 * mode_exp(e, 2) + 1)) /
+              (mesh_nonuniform(m) ? 1.0 : m.vol);
 #pragma unroll
     for (int D = 0; D < 3; ++D) {
       tix[D * NM + e] = tmode_index(mode_exp(e, tan1(D)), mode_exp(e, tan2(D)));
@@ -390,7 +438,9 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
       dL1[d][n] = dleg<R>(n, x);
     }
   }
-  const R sc[3] = {mesh_sc<R>(m, 0), mesh_sc<R>(m, 1), mesh_sc<R>(m, 2)};
+  const int icell = (i0 + cb < nx) ? i0 + cb : nx - 1;
+  const R sc[3] = {cell_sc<R>(m, 0, icell), cell_sc<R>(m, 1, j), cell_sc<R>(m, 2, k)};
+  const R cvol = mesh_nonuniform(m) ? cell_w<R>(m, 0, icell) * cell_w<R>(m, 1, j) * cell_w<R>(m, 2, k) : mesh_vol<R>(m);
   R Fw[3][5], Ftw[3][5];  // w |K| (2/h_d) F_d, same for F_t
   {
     R q[5], dq[3][5];
@@ -415,7 +465,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
     bool ok = true;
     if (active) ok = interior_flux(q, dq, gp, F, Ft);
     if (active && !ok) atomicOr(flag, 1u);
-    const R w = active ? gauss_wr<R>(NQ, pa[0]) * gauss_wr<R>(NQ, pa[1]) * gauss_wr<R>(NQ, pa[2]) * mesh_vol<R>(m) : R(0);
+    const R w = active ? gauss_wr<R>(NQ, pa[0]) * gauss_wr<R>(NQ, pa[1]) * gauss_wr<R>(NQ, pa[2]) * cvol : R(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d)
 #pragma unroll
@@ -485,7 +535,9 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
     }
     // M^-1 and the stage increments in the flux precision R; the
     // accumulation into the stored FP64 state is the one FP64 operation.
-    const R iM = (R)invM[mm];
+    R iM = (R)invM[mm];
+    if (mesh_nonuniform(m))  // 1/|K| = (2/h_x)(2/h_y)(2/h_z) / 8
+      iM *= cell_sc<R>(m, 0, i) * cell_sc<R>(m, 1, j) * cell_sc<R>(m, 2, k) * R(0.125);
     const R Lv = sF * iM, Ltv = sT * iM;
     if (MODE == MODE_RESIDUAL) {
       io.L[idx] = (double)Lv;
@@ -524,21 +576,26 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NV], double* __
 }
 
 template <int NM>
-__global__ void __launch_bounds__(RED_THREADS) k_totals_part(const double* __restrict__ Q, long long nc,
+__global__ void __launch_bounds__(RED_THREADS) k_totals_part(const double* __restrict__ Q, const MeshDev m,
                                                              double* __restrict__ part) {
+  const long long nc = m.ncell;
   double acc[5] = {0, 0, 0, 0, 0};
-  for (long long c = (long long)blockIdx.x * RED_THREADS + threadIdx.x; c < nc; c += (long long)gridDim.x * RED_THREADS)
+  for (long long c = (long long)blockIdx.x * RED_THREADS + threadIdx.x; c < nc; c += (long long)gridDim.x * RED_THREADS) {
+    const double wc = cell_weight(m, c);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] += Q[(size_t)(v * NM) * nc + c];
+    for (int v = 0; v < 5; ++v) acc[v] += wc * Q[(size_t)(v * NM) * nc + c];
+  }
   block_reduce_store<5>(acc, part);
 }
 
 template <int ORDER, int NQ>
-__global__ void __launch_bounds__(RED_THREADS) k_ek_part(const double* __restrict__ Q, long long nc,
+__global__ void __launch_bounds__(RED_THREADS) k_ek_part(const double* __restrict__ Q, const MeshDev m,
                                                          double* __restrict__ part) {
   constexpr int NM = n_modes(ORDER);
+  const long long nc = m.ncell;
   double acc[1] = {0};
   for (long long c = (long long)blockIdx.x * RED_THREADS + threadIdx.x; c < nc; c += (long long)gridDim.x * RED_THREADS) {
+    const double wc = cell_weight(m, c);
     double co[4][NM];
 #pragma unroll
     for (int v = 0; v < 4; ++v)
@@ -558,8 +615,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_ek_part(const double* __restric
 #pragma unroll
             for (int v = 0; v < 4; ++v) qv[v] += co[v][mm] * B;
           }
-          acc[0] += gauss_w(NQ, a) * gauss_w(NQ, b) * gauss_w(NQ, cz) * 0.5 *
-                    (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]) / qv[0];
+          acc[0] += wc * (gauss_w(NQ, a) * gauss_w(NQ, b) * gauss_w(NQ, cz) * 0.5 *
+                          (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]) / qv[0]);
         }
   }
   block_reduce_store<1>(acc, part);
@@ -568,13 +625,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_ek_part(const double* __restric
 // Enstrophy integral sum_cells sum_p w |K| rho |omega|^2 / 2 at the n_q^3
 // cell points (Sec. 5.3): omega = curl U, grad U = (grad m - U grad rho)/rho.
 template <int ORDER, int NQ>
-__global__ void __launch_bounds__(RED_THREADS) k_enstrophy_part(const double* __restrict__ Q, long long nc,
-                                                                double sx, double sy, double sz,
+__global__ void __launch_bounds__(RED_THREADS) k_enstrophy_part(const double* __restrict__ Q, const MeshDev m,
                                                                 double* __restrict__ part) {
   constexpr int NM = n_modes(ORDER);
+  const long long nc = m.ncell;
   double acc[1] = {0};
-  const double sc[3] = {sx, sy, sz};
   for (long long c = (long long)blockIdx.x * RED_THREADS + threadIdx.x; c < nc; c += (long long)gridDim.x * RED_THREADS) {
+    const double wc = cell_weight(m, c);
+    const int ci[3] = {(int)(c % m.nx), (int)((c / m.nx) % m.ny), (int)(c / ((long long)m.nx * m.ny))};
+    const double sc[3] = {cell_sc<double>(m, 0, ci[0]), cell_sc<double>(m, 1, ci[1]), cell_sc<double>(m, 2, ci[2])};
     double co[4][NM];
 #pragma unroll
     for (int v = 0; v < 4; ++v)
@@ -609,7 +668,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_enstrophy_part(const double* __
 #pragma unroll
             for (int i = 0; i < 3; ++i) du[d][i] = (g[d][1 + i] - q[1 + i] * ir * g[d][0]) * ir;
           const double w0 = du[1][2] - du[2][1], w1 = du[2][0] - du[0][2], w2 = du[0][1] - du[1][0];
-          acc[0] += gauss_w(NQ, a) * gauss_w(NQ, b) * gauss_w(NQ, cz) * 0.5 * q[0] * (w0 * w0 + w1 * w1 + w2 * w2);
+          acc[0] += wc * (gauss_w(NQ, a) * gauss_w(NQ, b) * gauss_w(NQ, cz) * 0.5 * q[0] * (w0 * w0 + w1 * w1 + w2 * w2));
         }
   }
   block_reduce_store<1>(acc, part);

@@ -5,8 +5,10 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "adjoint.h"
 #include "dg_kernels.cuh"
@@ -28,6 +30,10 @@ struct dghgks_ctx {
   int n[3] = {0, 0, 0};
   long long ncell = 0;
   double lo[3], hi[3], h[3], vol = 0;
+  double omega = 0;              // |Omega|
+  bool nonuniform = false;       // rectilinear mesh given by node coordinates
+  double* geo64 = nullptr;       // per axis: n_d widths, n_d values 2/width (device)
+  float* geo32 = nullptr;        // the same in FP32
   int order = 0, nq = 0, nm = 0, nt = 0, precision = 0;
   double gamma = 1.4, K = 2.0, mu = 0, Pr = 1, tau_eps = 0;
   void* Qs = nullptr;   // Q* (stage-1 output), flux precision
@@ -103,6 +109,12 @@ MeshDev mesh_dev(const dghgks_ctx* c) {
   }
   m.vol = c->vol;
   m.vol_f = (float)c->vol;
+  int off = 0;
+  for (int d = 0; d < 3; ++d) {
+    m.geo64[d] = c->nonuniform ? c->geo64 + off : nullptr;
+    m.geo32[d] = c->nonuniform ? c->geo32 + off : nullptr;
+    off += 2 * c->n[d];
+  }
   return m;
 }
 
@@ -210,14 +222,13 @@ struct Impl {
 
   static void enstrophy(dghgks_ctx* c, const double* Q, cudaStream_t s) {
     ProfScope ps(c, 6, s);
-    k_enstrophy_part<ORDER, NQ><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, c->ncell, 2.0 / c->h[0], 2.0 / c->h[1],
-                                                                    2.0 / c->h[2], c->part);
+    k_enstrophy_part<ORDER, NQ><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, mesh_dev(c), c->part);
     c->launches += 1;
   }
 
   static void ek(dghgks_ctx* c, const double* Q, cudaStream_t s) {
     ProfScope ps(c, 6, s);
-    k_ek_part<ORDER, NQ><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, c->ncell, c->part);
+    k_ek_part<ORDER, NQ><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, mesh_dev(c), c->part);
     c->launches += 1;
   }
 };
@@ -256,17 +267,24 @@ const Ops* select_ops(int precision, int order, int nq) {
 
 template <int NM>
 __global__ void __launch_bounds__(RED_THREADS) k_l2diff_part(const double* __restrict__ A, const double* __restrict__ B,
-                                                             int var, long long nc, double* __restrict__ part) {
+                                                             int var, const MeshDev m, double* __restrict__ part) {
+  const long long nc = m.ncell;
   double acc[1] = {0};
-  for (long long c = (long long)blockIdx.x * RED_THREADS + threadIdx.x; c < nc; c += (long long)gridDim.x * RED_THREADS)
+  for (long long c = (long long)blockIdx.x * RED_THREADS + threadIdx.x; c < nc; c += (long long)gridDim.x * RED_THREADS) {
+    const double wc = cell_weight(m, c);
 #pragma unroll
     for (int mm = 0; mm < NM; ++mm) {
       const size_t idx = (size_t)(var * NM + mm) * nc + c;
       const double d = A[idx] - B[idx];
-      acc[0] += d * d / (double)((2 * mode_exp(mm, 0) + 1) * (2 * mode_exp(mm, 1) + 1) * (2 * mode_exp(mm, 2) + 1));
+      acc[0] += wc * (d * d / (double)((2 * mode_exp(mm, 0) + 1) * (2 * mode_exp(mm, 1) + 1) * (2 * mode_exp(mm, 2) + 1)));
     }
+  }
   block_reduce_store<1>(acc, part);
 }
+
+// Final scale of the cell-sum reductions: the common cell volume on a uniform
+// mesh; 1 on a rectilinear one, whose partial sums carry each cell's volume.
+double vol_scale(const dghgks_ctx* c) { return c->nonuniform ? 1.0 : c->vol; }
 
 int after_launch(dghgks_ctx* c, const char* what) { return cuda_check(c, cudaGetLastError(), what); }
 
@@ -306,8 +324,18 @@ int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, dou
   if (!mesh) return fail(nullptr, DGHGKS_EARG, "mesh is NULL");
   if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || mesh->ny > 65535 || mesh->nz > 65535)
     return fail(nullptr, DGHGKS_EARG, "bad mesh size %d x %d x %d", mesh->nx, mesh->ny, mesh->nz);
+  const int n3[3] = {mesh->nx, mesh->ny, mesh->nz};
+  bool nonuniform = false;
   for (int d = 0; d < 3; ++d) {
-    if (!(mesh->hi[d] > mesh->lo[d])) return fail(nullptr, DGHGKS_EARG, "mesh hi <= lo along axis %d", d);
+    if (mesh->nodes[d]) {
+      nonuniform = true;
+      const double* x = mesh->nodes[d];
+      for (int q = 0; q < n3[d]; ++q)
+        if (!(std::isfinite(x[q]) && std::isfinite(x[q + 1]) && x[q + 1] > x[q]))
+          return fail(nullptr, DGHGKS_EARG, "mesh nodes along axis %d not strictly increasing at %d", d, q);
+    } else if (!(mesh->hi[d] > mesh->lo[d])) {
+      return fail(nullptr, DGHGKS_EARG, "mesh hi <= lo along axis %d", d);
+    }
     if (mesh->periodic[d] != 1) return fail(nullptr, DGHGKS_EUNSUP, "only periodic boundaries are supported");
   }
   if (!(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0)) return fail(nullptr, DGHGKS_EARG, "bad gas parameters");
@@ -328,12 +356,30 @@ int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, dou
   c->n[2] = mesh->nz;
   c->ncell = (long long)mesh->nx * mesh->ny * mesh->nz;
   c->vol = 1.0;
+  c->nonuniform = nonuniform;
+  // per-axis widths and 2/width of a rectilinear mesh (uniform axes filled
+  // with their common width)
+  std::vector<double> geo64;
+  std::vector<float> geo32;
   for (int d = 0; d < 3; ++d) {
-    c->lo[d] = mesh->lo[d];
-    c->hi[d] = mesh->hi[d];
-    c->h[d] = (mesh->hi[d] - mesh->lo[d]) / c->n[d];
+    const double* x = mesh->nodes[d];
+    c->lo[d] = x ? x[0] : mesh->lo[d];
+    c->hi[d] = x ? x[n3[d]] : mesh->hi[d];
+    c->h[d] = (c->hi[d] - c->lo[d]) / c->n[d];
     c->vol *= c->h[d];
+    if (nonuniform) {
+      const size_t off = geo64.size();
+      geo64.resize(off + 2 * n3[d]);
+      for (int q = 0; q < n3[d]; ++q) {
+        const double w = x ? x[q + 1] - x[q] : c->h[d];
+        geo64[off + q] = w;
+        geo64[off + n3[d] + q] = 2.0 / w;
+      }
+    }
   }
+  c->omega = nonuniform ? (c->hi[0] - c->lo[0]) * (c->hi[1] - c->lo[1]) * (c->hi[2] - c->lo[2])
+                        : c->vol * (double)c->ncell;
+  for (double v : geo64) geo32.push_back((float)v);
   c->order = order;
   c->nq = nq;
   c->nm = n_modes(order);
@@ -358,6 +404,16 @@ int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, dou
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->red, sizeof(double) * 8), "cudaMalloc(red)");
   if (!rc) rc = cuda_check(c, cudaMallocHost(&c->red_host, sizeof(double) * 8), "cudaMallocHost");
   if (!rc) rc = cuda_check(c, cudaMemset(c->flag, 0, sizeof(unsigned)), "cudaMemset(flag)");
+  if (!rc && nonuniform) {
+    rc = cuda_check(c, cudaMalloc(&c->geo64, sizeof(double) * geo64.size()), "cudaMalloc(mesh widths)");
+    if (!rc) rc = cuda_check(c, cudaMalloc(&c->geo32, sizeof(float) * geo32.size()), "cudaMalloc(mesh widths)");
+    if (!rc)
+      rc = cuda_check(c, cudaMemcpy(c->geo64, geo64.data(), sizeof(double) * geo64.size(), cudaMemcpyHostToDevice),
+                      "copy mesh widths");
+    if (!rc)
+      rc = cuda_check(c, cudaMemcpy(c->geo32, geo32.data(), sizeof(float) * geo32.size(), cudaMemcpyHostToDevice),
+                      "copy mesh widths");
+  }
   if (rc) {
     snprintf(g_init_err, sizeof(g_init_err), "%s", c->err);
     dghgks_destroy(c);
@@ -386,6 +442,8 @@ void dghgks_destroy(dghgks_ctx* c) {
   cudaFree(c->adjH);
   cudaFree(c->adjLam);
   cudaFree(c->adjMu);
+  cudaFree(c->geo64);
+  cudaFree(c->geo32);
   if (c->red_host) cudaFreeHost(c->red_host);
   delete c;
 }
@@ -477,12 +535,13 @@ int dghgks_totals(dghgks_ctx* c, const double* Q, double* out, void* stream) {
   if (!c) return DGHGKS_EARG;
   if (!Q || !out) return fail(c, DGHGKS_EARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const MeshDev m = mesh_dev(c);
   switch (c->nm) {
-    case 4: k_totals_part<4><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, c->ncell, c->part); break;
-    case 10: k_totals_part<10><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, c->ncell, c->part); break;
-    default: k_totals_part<20><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, c->ncell, c->part); break;
+    case 4: k_totals_part<4><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, m, c->part); break;
+    case 10: k_totals_part<10><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, m, c->part); break;
+    default: k_totals_part<20><<<kRedBlocks, RED_THREADS, 0, s>>>(Q, m, c->part); break;
   }
-  k_reduce_final<5><<<1, RED_THREADS, 0, s>>>(c->part, kRedBlocks, c->vol, c->red);
+  k_reduce_final<5><<<1, RED_THREADS, 0, s>>>(c->part, kRedBlocks, vol_scale(c), c->red);
   c->launches += 2;
   if (int rc = after_launch(c, "totals launch")) return rc;
   if (int rc = cuda_check(c, cudaMemcpyAsync(c->red_host, c->red, 5 * sizeof(double), cudaMemcpyDeviceToHost, s),
@@ -495,8 +554,7 @@ int dghgks_totals(dghgks_ctx* c, const double* Q, double* out, void* stream) {
 
 static int enqueue_ek(dghgks_ctx* c, const double* Q, double rho0, double* dst_dev, cudaStream_t s) {
   c->ops->ek(c, Q, s);
-  const double omega = c->vol * (double)c->ncell;
-  k_reduce_final<1><<<1, RED_THREADS, 0, s>>>(c->part, kRedBlocks, c->vol / (rho0 * omega), dst_dev);
+  k_reduce_final<1><<<1, RED_THREADS, 0, s>>>(c->part, kRedBlocks, vol_scale(c) / (rho0 * c->omega), dst_dev);
   c->launches += 1;
   return after_launch(c, "kinetic energy launch");
 }
@@ -521,8 +579,8 @@ int dghgks_enstrophy_dissipation(dghgks_ctx* c, const double* Q, double rho0, do
   if (!(rho0 > 0)) return fail(c, DGHGKS_EARG, "rho0 must be > 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   c->ops->enstrophy(c, Q, s);
-  const double omega = c->vol * (double)c->ncell;
-  k_reduce_final<1><<<1, RED_THREADS, 0, s>>>(c->part, kRedBlocks, 2.0 * c->mu * c->vol / (rho0 * omega), c->red);
+  k_reduce_final<1><<<1, RED_THREADS, 0, s>>>(c->part, kRedBlocks, 2.0 * c->mu * vol_scale(c) / (rho0 * c->omega),
+                                              c->red);
   c->launches += 1;
   if (int rc = after_launch(c, "enstrophy launch")) return rc;
   if (int rc = cuda_check(c, cudaMemcpyAsync(c->red_host, c->red, sizeof(double), cudaMemcpyDeviceToHost, s),
@@ -537,12 +595,13 @@ int dghgks_l2_diff(dghgks_ctx* c, const double* A, const double* B, int var, dou
   if (!c) return DGHGKS_EARG;
   if (!A || !B || !out || var < 0 || var > 4) return fail(c, DGHGKS_EARG, "bad argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const MeshDev m = mesh_dev(c);
   switch (c->nm) {
-    case 4: k_l2diff_part<4><<<kRedBlocks, RED_THREADS, 0, s>>>(A, B, var, c->ncell, c->part); break;
-    case 10: k_l2diff_part<10><<<kRedBlocks, RED_THREADS, 0, s>>>(A, B, var, c->ncell, c->part); break;
-    default: k_l2diff_part<20><<<kRedBlocks, RED_THREADS, 0, s>>>(A, B, var, c->ncell, c->part); break;
+    case 4: k_l2diff_part<4><<<kRedBlocks, RED_THREADS, 0, s>>>(A, B, var, m, c->part); break;
+    case 10: k_l2diff_part<10><<<kRedBlocks, RED_THREADS, 0, s>>>(A, B, var, m, c->part); break;
+    default: k_l2diff_part<20><<<kRedBlocks, RED_THREADS, 0, s>>>(A, B, var, m, c->part); break;
   }
-  k_reduce_final<1><<<1, RED_THREADS, 0, s>>>(c->part, kRedBlocks, c->vol, c->red);
+  k_reduce_final<1><<<1, RED_THREADS, 0, s>>>(c->part, kRedBlocks, vol_scale(c), c->red);
   c->launches += 2;
   if (int rc = after_launch(c, "l2 diff launch")) return rc;
   if (int rc = cuda_check(c, cudaMemcpyAsync(c->red_host, c->red, sizeof(double), cudaMemcpyDeviceToHost, s),
@@ -615,6 +674,7 @@ int dghgks_profile_read(dghgks_ctx* c, double* ms, int64_t* launches) {
 
 static int adj_prepare(dghgks_ctx* c) {
   if (c->precision != DGHGKS_FP64) return fail(c, DGHGKS_EUNSUP, "the adjoint needs an FP64 context");
+  if (c->nonuniform) return fail(c, DGHGKS_EUNSUP, "the adjoint supports uniform meshes only");
   if (c->order > 2) return fail(c, DGHGKS_EUNSUP, "the adjoint supports orders 1 and 2");
   if (c->adjH) return DGHGKS_OK;
   const size_t nc = (size_t)c->ncell;
@@ -699,10 +759,10 @@ int dghgks_adjoint_step(dghgks_ctx* c, const double* Qn, const double* lam_next,
 int dghgks_kinetic_energy_vjp(dghgks_ctx* c, const double* Q, double rho0, double* dEk_dQ, void* stream) {
   if (!c) return DGHGKS_EARG;
   if (c->order > 2) return fail(c, DGHGKS_EUNSUP, "the adjoint supports orders 1 and 2");
+  if (c->nonuniform) return fail(c, DGHGKS_EUNSUP, "the adjoint supports uniform meshes only");
   if (!Q || !dEk_dQ || dEk_dQ == Q) return fail(c, DGHGKS_EARG, "bad argument");
   if (!(rho0 > 0)) return fail(c, DGHGKS_EARG, "rho0 must be > 0");
-  const double omega = c->vol * (double)c->ncell;
-  adjoint_ek_vjp(c->order, c->nq, Q, c->ncell, c->vol / (rho0 * omega), dEk_dQ, static_cast<cudaStream_t>(stream));
+  adjoint_ek_vjp(c->order, c->nq, Q, c->ncell, c->vol / (rho0 * c->omega), dEk_dQ, static_cast<cudaStream_t>(stream));
   c->launches += 1;
   return after_launch(c, "E_k VJP launch");
 }

@@ -125,6 +125,7 @@ extern "C" int dghgks_residual_static(const dghgks_mesh* mesh, int order, double
   for (int d = 0; d < 3; ++d) {
     if (!(mesh->hi[d] > mesh->lo[d])) return DGHGKS_EARG;
     if (mesh->periodic[d] != 1) return DGHGKS_EUNSUP;
+    if (mesh->nodes[d]) return DGHGKS_EUNSUP;  // uniform meshes only
   }
   if (!(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0) || !(dt > 0.0)) return DGHGKS_EARG;
   const int nq = (opts && opts->n_q) ? opts->n_q : order + 1;
@@ -159,6 +160,10 @@ extern "C" int dghgks_residual_static(const dghgks_mesh* mesh, int order, double
     m.area_f[k] = (float)(m.vol / m.h[k]);
   }
   m.vol_f = (float)m.vol;
+  for (int k = 0; k < 3; ++k) {
+    m.geo64[k] = nullptr;
+    m.geo32[k] = nullptr;
+  }
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the flag must start at zero: it keeps the previous call's value

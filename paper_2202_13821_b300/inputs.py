@@ -74,13 +74,43 @@ def _xp(device):
     return _NP if device is None else _TH(device)
 
 
-def _centres(xp, n, lo, hi):
-    h = [(hi[d] - lo[d]) / n[d] for d in range(3)]
-    x = lo[0] + (xp.arange(n[0]) + 0.5) * h[0]
-    y = lo[1] + (xp.arange(n[1]) + 0.5) * h[1]
-    z = lo[2] + (xp.arange(n[2]) + 0.5) * h[2]
+def mapped_nodes(n, lo=0.0, hi=2.0, amp=0.05):
+    """Node coordinates x_q = xi_q + amp sin(pi xi_q) of the non-uniform mesh of
+    Sec. 5.1 (xi_q uniform on [lo, hi]; on [0, 2] the end nodes stay fixed)."""
+    xi = lo + (hi - lo) * np.arange(n + 1) / n
+    return xi + amp * np.sin(np.pi * xi)
+
+
+def random_nodes(n, lo=0.0, hi=2.0, spread=0.3, seed=SEED):
+    """n + 1 increasing nodes on [lo, hi] whose cell widths are the mean width
+    times independent uniform factors in [1 - spread, 1 + spread] (renormalised)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = 1.0 + spread * rng.uniform(-1.0, 1.0, n)
+    x = np.concatenate([[0.0], np.cumsum(w)])
+    x = lo + (hi - lo) * x / x[-1]
+    x[-1] = hi
+    return x
+
+
+def _centres(xp, n, lo, hi, nodes=None):
+    cen, h = [], []
+    for d in range(3):
+        nd = None if nodes is None else nodes[d]
+        if nd is None:
+            hd = (hi[d] - lo[d]) / n[d]
+            cen.append(lo[d] + (xp.arange(n[d]) + 0.5) * hd)
+            h.append(hd)
+        else:
+            nd = np.asarray(nd, dtype=np.float64)
+            c, w = 0.5 * (nd[1:] + nd[:-1]), nd[1:] - nd[:-1]
+            if xp is not _NP:
+                c, w = (xp.t.from_numpy(np.ascontiguousarray(v)).to(xp.device) for v in (c, w))
+            cen.append(c)
+            h.append(w)
     # broadcastable axes: X varies along the last (x) axis, Z along the first
-    return (x[None, None, :], y[None, :, None], z[:, None, None]), h
+    shp = ((None, None, slice(None)), (None, slice(None), None), (slice(None), None, None))
+    h = [v if np.isscalar(v) else v[shp[d]] for d, v in enumerate(h)]
+    return tuple(cen[d][shp[d]] for d in range(3)), h
 
 
 def _cons_from_prim(xp, rho, U, V, W, p, gamma):
@@ -105,7 +135,8 @@ def tgv_prim(xp, x, y, z, V0=1.0, rho0=1.0, p0=None, Ma=0.1, gamma=1.4, isotherm
     return rho, U, V, 0.0, p
 
 
-def modal_state(prim_fn, n, order, lo, hi, gamma=1.4, perturb=0.0, seed=SEED, device=None, prim_kw=None):
+def modal_state(prim_fn, n, order, lo, hi, gamma=1.4, perturb=0.0, seed=SEED, device=None, prim_kw=None,
+                nodes=None):
     """Cell-centre sample + first-derivative linear modes + seeded perturbation.
 
     The linear coefficient of P_1(xi_d) is (h_d / 2) dq/dx_d at the centre
@@ -113,11 +144,13 @@ def modal_state(prim_fn, n, order, lo, hi, gamma=1.4, perturb=0.0, seed=SEED, de
     of the initial condition over h_d / 1000.  ``perturb`` scales a standard
     normal perturbation (numpy PCG64 stream ``seed``) added to every
     coefficient, relative to the largest |cell mean| of each variable.
+    ``nodes``: optional per-axis node coordinates of a rectilinear mesh
+    (then h_d is each cell's width).
     """
     xp = _xp(device)
     kw = prim_kw or {}
     n = (int(n),) * 3 if np.isscalar(n) else tuple(int(v) for v in n)
-    (X, Y, Z), h = _centres(xp, n, lo, hi)
+    (X, Y, Z), h = _centres(xp, n, lo, hi, nodes)
     Q = xp.zeros((5, n_modes(order), n[2], n[1], n[0]))
     Q[:, 0] = _cons_from_prim(xp, *prim_fn(xp, X, Y, Z, **kw), gamma)
     if order >= 1:
@@ -138,9 +171,9 @@ def modal_state(prim_fn, n, order, lo, hi, gamma=1.4, perturb=0.0, seed=SEED, de
     return Q
 
 
-def advection_state(n, order, perturb=0.0, seed=SEED, gamma=1.4, amp=0.2, device=None):
+def advection_state(n, order, perturb=0.0, seed=SEED, gamma=1.4, amp=0.2, device=None, nodes=None):
     return modal_state(advection_prim, n, order, (0.0,) * 3, (2.0,) * 3, gamma, perturb, seed, device,
-                       dict(amp=amp))
+                       dict(amp=amp), nodes)
 
 
 def tgv_state(n, order, perturb=0.0, seed=SEED, gamma=1.4, Ma=0.1, isothermal=False, device=None):

@@ -50,9 +50,10 @@ def per_var_err(a, b):
     return np.abs(a - b).max(axis=1) / scale
 
 
-def make(api, orc, n, lo, hi, order, nq, mu=0.0, Pr=1.0, tau_eps=0.0, precision=0):
-    s = api.Solver(n, lo, hi, order=order, mu=mu, Pr=Pr, n_q=nq, precision=precision, tau_eps=tau_eps)
-    pb = orc.Problem(order=order, nq=nq, n=tuple(n), lo=tuple(lo), hi=tuple(hi), mu=mu, Pr=Pr, tau_eps=tau_eps)
+def make(api, orc, n, lo, hi, order, nq, mu=0.0, Pr=1.0, tau_eps=0.0, precision=0, nodes=None):
+    s = api.Solver(n, lo, hi, order=order, mu=mu, Pr=Pr, n_q=nq, precision=precision, tau_eps=tau_eps, nodes=nodes)
+    pb = orc.Problem(order=order, nq=nq, n=tuple(n), lo=tuple(lo), hi=tuple(hi), mu=mu, Pr=Pr, tau_eps=tau_eps,
+                     nodes=nodes)
     return s, pb
 
 
@@ -204,3 +205,111 @@ def test_totals_and_kinetic_energy(torch, api, orc):
     want = math.sqrt(np.sum(M[:, None, None, None] * (Q2[0] - Q[0]) ** 2))
     got = s.l2_diff(torch.from_numpy(Q2).cuda(), Qd, 0)
     assert abs(got - want) <= 1e-12 * want
+
+
+# ---- rectilinear (non-uniform) meshes ----
+
+def random_mesh(n, lo, hi, seed=40, spread=0.4):
+    from paper_2202_13821_b300 import inputs
+
+    return tuple(inputs.random_nodes(n[d], lo[d], hi[d], spread=spread, seed=seed + d) for d in range(3))
+
+
+@pytest.mark.parametrize("order,nq", [(1, 2), (2, 3), (2, 2), (3, 3), (3, 4)])
+@pytest.mark.parametrize("n", [(37, 5, 6), (3, 4, 2)])
+def test_rectilinear_residual(torch, api, orc, order, nq, n):
+    """Random cell widths (+-40%) on every axis; x spans two face tiles with a ragged tail."""
+    from paper_2202_13821_b300 import inputs
+
+    nodes = random_mesh(n, TGV["lo"], TGV["hi"])
+    s, pb = make(api, orc, n, order=order, nq=nq, mu=1 / 1600, Pr=0.72, nodes=nodes, **TGV)
+    Q = inputs.modal_state(inputs.tgv_prim, n, order, TGV["lo"], TGV["hi"], perturb=1e-3, nodes=nodes)
+    L, Lt, ref = residual_pair(torch, s, pb, orc, Q, 1.3e-3)
+    assert_residual_parity(L, Lt, ref)
+
+
+def test_rectilinear_mapped_mesh_one_axis(torch, api, orc):
+    """The mapped grid of Sec. 5.1 along y only (x, z uniform), random discontinuous state."""
+    from paper_2202_13821_b300 import inputs
+
+    n = (6, 9, 4)
+    nodes = (None, inputs.mapped_nodes(9), None)
+    s, pb = make(api, orc, n, lo=(0.0,) * 3, hi=(1.0, 2.0, 0.5), order=2, nq=3, mu=2e-3, Pr=0.72, tau_eps=0.01,
+                 nodes=nodes)
+    Q = inputs.random_state(n, 2, seed=17)
+    L, Lt, ref = residual_pair(torch, s, pb, orc, Q, 2e-3)
+    assert_residual_parity(L, Lt, ref)
+
+
+@pytest.mark.parametrize("order,nq", [(2, 3), (3, 4)])
+def test_rectilinear_step_parity(torch, api, orc, order, nq):
+    from paper_2202_13821_b300 import inputs
+
+    n = (6, 7, 5)
+    nodes = tuple(inputs.mapped_nodes(v) for v in n)
+    s, pb = make(api, orc, n, order=order, nq=nq, tau_eps=0.01, nodes=nodes, **ADV)
+    Q = inputs.advection_state(n, order, perturb=1e-3, nodes=nodes)
+    Qd = torch.from_numpy(Q).cuda()
+    s.step(Qd, 6e-3, 2)
+    s.status()
+    Qo = orc.step(pb, Q, 6e-3, 2)
+    assert per_var_err(Qd.cpu().numpy() - Q, Qo - Q).max() < RTOL
+
+
+def test_rectilinear_reductions(torch, api, orc):
+    from paper_2202_13821_b300 import inputs
+
+    n = (12, 10, 9)
+    nodes = random_mesh(n, TGV["lo"], TGV["hi"], seed=50)
+    s, pb = make(api, orc, n, order=2, nq=3, mu=1 / 1600, nodes=nodes, **TGV)
+    Q = inputs.modal_state(inputs.tgv_prim, n, 2, TGV["lo"], TGV["hi"], perturb=1e-3, nodes=nodes)
+    Qd = torch.from_numpy(Q).cuda()
+    np.testing.assert_allclose(s.totals(Qd), orc.totals(pb, Q), rtol=1e-13, atol=1e-13)
+    assert abs(s.kinetic_energy(Qd) - orc.kinetic_energy(pb, Q)) < 1e-14
+    e_gpu, e_orc = s.enstrophy_dissipation(Qd), orc.enstrophy_dissipation(pb, Q)
+    assert abs(e_gpu - e_orc) <= 1e-12 * abs(e_orc)
+    Q2 = Q.copy()
+    Q2[0] += 1e-3 * np.random.default_rng(2).standard_normal(Q2[0].shape)
+    w = [np.diff(x) for x in nodes]
+    vol = w[2][:, None, None] * w[1][None, :, None] * w[0][None, None, :]
+    md = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2), (1, 1, 0), (1, 0, 1), (0, 1, 1)]
+    norm = np.array([1.0 / np.prod([2 * e + 1 for e in m]) for m in md])
+    want = math.sqrt(np.sum(norm[:, None, None, None] * vol[None] * (Q2[0] - Q[0]) ** 2))
+    got = s.l2_diff(torch.from_numpy(Q2).cuda(), Qd, 0)
+    assert abs(got - want) <= 1e-12 * want
+
+
+def test_rectilinear_fp32_mixed_close_to_fp64(torch, api, orc):
+    from paper_2202_13821_b300 import inputs
+
+    n = (20, 12, 9)
+    nodes = random_mesh(n, TGV["lo"], TGV["hi"], seed=60)
+    Q = inputs.modal_state(inputs.tgv_prim, n, 2, TGV["lo"], TGV["hi"], perturb=1e-3, nodes=nodes)
+    out = []
+    for prec in (0, 1):
+        s = api.Solver(n, TGV["lo"], TGV["hi"], order=2, mu=1 / 1600, Pr=0.72, n_q=3, precision=prec, nodes=nodes)
+        L, Lt = s.residual(torch.from_numpy(Q).cuda(), 1.3e-3)
+        s.status()
+        out.append((L.cpu().numpy(), Lt.cpu().numpy()))
+    ref = oracle_residual(orc, orc.Problem(order=2, nq=3, n=n, mu=1 / 1600, Pr=0.72, nodes=nodes), Q, 1.3e-3)
+    for a, b, sc in ((out[1][0], out[0][0], ref[2]), (out[1][1], out[0][1], ref[3])):
+        err = np.abs(a - b).reshape(5, -1).max(axis=1)
+        scale = np.abs(sc).reshape(5, -1).max(axis=1)
+        assert np.all(err <= 2e-5 * scale), err / scale
+
+
+def test_rectilinear_rejected_where_unsupported(torch, api):
+    from paper_2202_13821_b300 import inputs
+
+    n = (4, 4, 4)
+    nodes = (inputs.mapped_nodes(4), None, None)
+    s = api.Solver(n, (0,) * 3, (2,) * 3, order=2, nodes=nodes)
+    Q = torch.from_numpy(inputs.advection_state(n, 2, nodes=nodes)).cuda()
+    dmu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(api.DghgksError) as e:
+        api.dghgks_residual_vjp(s.ctx, Q, 1e-3, Q.clone(), Q.clone(), torch.empty_like(Q), dmu)
+    assert e.value.code == -2
+    bad = inputs.mapped_nodes(4)[::-1].copy()
+    with pytest.raises(api.DghgksError) as e:
+        api.Solver(n, (0,) * 3, (2,) * 3, order=2, nodes=(bad, None, None))
+    assert e.value.code == -1
