@@ -54,6 +54,8 @@ struct MeshDev {
   float sc_f[3];    // 2 / h_d
   float area_f[3];  // |Gamma| of a face normal to d
   float vol_f;
+  double ivol;      // 1 / |K|
+  float ivol_f;
   // Rectilinear (non-uniform) meshes: per axis d, the n_d cell widths followed
   // by the n_d values 2 / width, in FP64 and FP32.  All null on a uniform mesh,
   // where the scalars above hold.
@@ -88,6 +90,14 @@ __device__ __forceinline__ R mesh_vol(const MeshDev& m) {
 template <>
 __device__ __forceinline__ float mesh_vol<float>(const MeshDev& m) {
   return m.vol_f;
+}
+template <class R>
+__device__ __forceinline__ R mesh_ivol(const MeshDev& m) {
+  return (R)m.ivol;
+}
+template <>
+__device__ __forceinline__ float mesh_ivol<float>(const MeshDev& m) {
+  return m.ivol_f;
 }
 template <class R>
 __device__ __forceinline__ const R* mesh_geo(const MeshDev& m, int d) {
@@ -148,6 +158,7 @@ struct FaceSmem {
   static constexpr size_t coef = sizeof(R) * NC * FB;  // one side
   static constexpr size_t fs = sizeof(R) * 10 * NP * FB;
   static constexpr size_t bytes = 2 * coef + fs;
+  static_assert(sizeof(R) * FB * 10 * NT <= 2 * coef, "face moments must fit the staging area");
 };
 
 __device__ __forceinline__ int wrapm(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
@@ -155,7 +166,9 @@ __device__ __forceinline__ int wrapm(int i, int n) { return i < 0 ? i + n : (i >
 // ---------------------------------------------------------------------------
 // Face kernel
 // ---------------------------------------------------------------------------
-template <class R, int ORDER, int NQ, int D, class Tin>
+// FTO (the stage-2 pass of S2O4, which needs L_t(Q*) only): the F_t moments
+// alone are projected and stored; F is left to dead-code elimination.
+template <class R, int ORDER, int NQ, int D, class Tin, bool FTO = false>
 __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>()))
     k_face(const Tin* __restrict__ Q, R* __restrict__ G, const GasPar<R> gp, const MeshDev m,
            unsigned* __restrict__ flag) {
@@ -271,11 +284,13 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   ok = iface_finish(sums, gp, Fl, Ftl) && ok;
   if (active && !ok) atomicOr(flag, 1u);
   const R w = active ? gauss_wr<R>(NQ, a) * gauss_wr<R>(NQ, b) * face_area<R>(m, D, cidx[T1], cidx[T2]) : R(0);
-  Fs[0][p][f] = w * Fl[0];
-  Fs[1 + A0][p][f] = w * Fl[1];
-  Fs[1 + A1][p][f] = w * Fl[2];
-  Fs[1 + A2][p][f] = w * Fl[3];
-  Fs[4][p][f] = w * Fl[4];
+  if (!FTO) {
+    Fs[0][p][f] = w * Fl[0];
+    Fs[1 + A0][p][f] = w * Fl[1];
+    Fs[1 + A1][p][f] = w * Fl[2];
+    Fs[1 + A2][p][f] = w * Fl[3];
+    Fs[4][p][f] = w * Fl[4];
+  }
   Fs[5][p][f] = w * Ftl[0];
   Fs[6 + A0][p][f] = w * Ftl[1];
   Fs[6 + A1][p][f] = w * Ftl[2];
@@ -283,24 +298,37 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   Fs[9][p][f] = w * Ftl[4];
   __syncthreads();
 
-  // tangential projection G[D][c][t][face] = sum_p Fs[c][p] phi_t(p): the
+  // tangential projection G[D][face][c][t] = sum_p Fs[c][p] phi_t(p): the
   // thread with point index p takes components c = p, p + NP, ...; the
-  // Legendre products phi_t(p) are compile-time constants.
-  if (active) {
-    const size_t face = ((size_t)k * ny + j) * nx + i;
-    for (int c = p; c < 10; c += NP) {
-      R fv[NP];
+  // Legendre products phi_t(p) are compile-time constants.  The CTA's faces
+  // are consecutive in G (face-major layout), so the moments are gathered in
+  // shared memory (over the coefficient staging area, free after the
+  // barrier above) and written as one contiguous block.
+  R(*Gs)[10][NT] = reinterpret_cast<R(*)[10][NT]>(smem_raw);
+  for (int c = (FTO ? 5 : 0) + p; c < 10; c += NP) {
+    R fv[NP];
 #pragma unroll
-      for (int pp = 0; pp < NP; ++pp) fv[pp] = Fs[c][pp][f];
+    for (int pp = 0; pp < NP; ++pp) fv[pp] = Fs[c][pp][f];
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        R s = R(0);
+    for (int t = 0; t < NT; ++t) {
+      R s = R(0);
 #pragma unroll
-        for (int pp = 0; pp < NP; ++pp)
-          s += fv[pp] * (leg<R>(tmode_p(t), gauss_xr<R>(NQ, pp / NQ)) * leg<R>(tmode_q(t), gauss_xr<R>(NQ, pp % NQ)));
-        G[((size_t)(D * 10 + c) * NT + t) * nc + face] = s;
-      }
+      for (int pp = 0; pp < NP; ++pp)
+        s += fv[pp] * (leg<R>(tmode_p(t), gauss_xr<R>(NQ, pp / NQ)) * leg<R>(tmode_q(t), gauss_xr<R>(NQ, pp % NQ)));
+      Gs[f][c][t] = s;
     }
+  }
+  __syncthreads();
+  const int nf = nx - i0 < FB ? nx - i0 : FB;
+  R* const dst = G + ((size_t)D * nc + ((size_t)k * ny + j) * nx + i0) * (10 * NT);
+  const R* const src = &Gs[0][0][0];
+  if (FTO) {
+    for (int e = tid; e < nf * 5 * NT; e += FB * NP) {
+      const int ff = e / (5 * NT), r = e % (5 * NT);
+      dst[ff * (10 * NT) + 5 * NT + r] = src[ff * (10 * NT) + 5 * NT + r];
+    }
+  } else {
+    for (int e = tid; e < nf * 10 * NT; e += FB * NP) dst[e] = src[e];
   }
 }
 
@@ -332,8 +360,9 @@ struct CellSmem {
   using LY = CellLayout<ORDER, NQ>;
   static constexpr int NM = LY::NM, NC = 5 * NM, CB = LY::CB;
   static constexpr size_t coef = sizeof(R) * NC * CB;
-  static constexpr size_t red = sizeof(R) * CB * LY::GW * 2 * LY::NOP;
-  static constexpr size_t tabs = sizeof(double) * NM + sizeof(int) * 6 * NM;
+  // cross-warp partial sums (only when a cell spans two warps)
+  static constexpr size_t red = LY::GW == 1 ? 0 : sizeof(R) * CB * LY::GW * 2 * LY::NOP;
+  static constexpr size_t tabs = sizeof(R) * NM + sizeof(int) * 6 * NM;
   static constexpr size_t bytes = coef + red + tabs;
 };
 
@@ -383,8 +412,13 @@ struct StageIO {
   double* Qn;
 };
 
+// Resident CTAs of k_cell per SM requested from the compiler (FP32): 2 gives
+// the register cap 128.
+#ifndef CELL_MIN_CTAS_F32
+#define CELL_MIN_CTAS_F32 2
+#endif
 template <class R, int ORDER, int NQ, int MODE, class Tin>
-__global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) == 4 ? CELL_MIN_CTAS_F32 : 1)
     k_cell(const Tin* __restrict__ Qin, const R* __restrict__ G, const StageIO<R> io, const GasPar<R> gp,
            const MeshDev m, const double dt, unsigned* __restrict__ flag) {
   using LY = CellLayout<ORDER, NQ>;
@@ -393,8 +427,8 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
   constexpr int NOUT = LY::NOUT, NOP = LY::NOP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R(*coef)[CB] = reinterpret_cast<R(*)[CB]>(smem_raw);
-  R(*red)[GW][2][NOP] = reinterpret_cast<R(*)[GW][2][NOP]>(smem_raw + S::coef);
-  double* invM = reinterpret_cast<double*>(smem_raw + S::coef + S::red);
+  R(*red)[GW][2][NOP] = reinterpret_cast<R(*)[GW][2][NOP]>(smem_raw + S::coef);  // GW > 1 only
+  R* invM = reinterpret_cast<R*>(smem_raw + S::coef + S::red);
   int* tix = reinterpret_cast<int*>(invM + NM);  // [3][NM] tangential index, then [3][NM] parity sign
 
   const int tid = threadIdx.x, nthr = LY::WARPS * 32;
@@ -414,8 +448,8 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
   for (int e = tid; e < NM; e += nthr) {
     // (2a+1)(2b+1)(2c+1) / |K|; on a rectilinear mesh the 1/|K| of each cell
     // is applied in the epilogue
-    invM[e] = (double)((2 * mode_exp(e, 0) + 1) * (2 * mode_exp(e, 1) + 1) * (2 * mode_exp(e, 2) + 1)) /
-              (mesh_nonuniform(m) ? 1.0 : m.vol);
+    invM[e] = (R)((2 * mode_exp(e, 0) + 1) * (2 * mode_exp(e, 1) + 1) * (2 * mode_exp(e, 2) + 1)) *
+              (mesh_nonuniform(m) ? R(1) : mesh_ivol<R>(m));
 #pragma unroll
     for (int D = 0; D < 3; ++D) {
       tix[D * NM + e] = tmode_index(mode_exp(e, tan1(D)), mode_exp(e, tan2(D)));
@@ -475,52 +509,18 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
       }
   }
 
-  // ---- volume projection: sum over the group's points of Fw . grad B_n (n >= 1),
-  // PG outputs at a time (lane lg ends with output c0 + lg of each chunk) ----
-#pragma unroll
-  for (int kind = 0; kind < 2; ++kind) {
-#pragma unroll
-    for (int c0 = 0; c0 < NOP; c0 += PG) {
-      R val[PG];
-#pragma unroll
-      for (int oo = 0; oo < PG; ++oo) {
-        const int o = c0 + oo;
-        R c = R(0);
-        if (o < NOUT) {
-          const int v = o / (NM - 1), n = 1 + o % (NM - 1);
-          const int e0 = mode_exp(n, 0), e1 = mode_exp(n, 1), e2 = mode_exp(n, 2);
-          const R(&Fk)[3][5] = kind == 0 ? Fw : Ftw;
-          if (e0 > 0) c += Fk[0][v] * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
-          if (e1 > 0) c += Fk[1][v] * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
-          if (e2 > 0) c += Fk[2][v] * (L1[0][e0] * L1[1][e1] * dL1[2][e2]);
-        }
-        val[oo] = c;
-      }
-      R outv[1];
-      group_reduce<PG, PG>(val, outv, lg);
-      red[cb][gw][kind][c0 + lg] = outv[0];
-    }
-  }
-  __syncthreads();
-
-  // ---- face assembly, inverse mass matrix, stage epilogue (FP64) ----
-  for (int o = tid; o < CB * NC; o += nthr) {
-    const int cc = o % CB, rest = o / CB, mm = rest % NM, v = rest / NM;
-    const int i = i0 + cc;
-    if (i >= nx) continue;
+  // One output (variable v, mode n) of the cell at x index i: the six faces'
+  // moments with the sign/parity of Eq. (operator), M^-1, and the stage
+  // epilogue in the flux precision R; the accumulation into the stored FP64
+  // state is the one FP64 operation.
+  const R h = (R)dt, h2 = (R)(dt * dt);
+  auto finish = [&](int v, int n, int i, int cc, R sF, R sT) {
     const size_t cell = row + i;
-    const size_t idx = (size_t)(v * NM + mm) * nc + cell;
-    R sF = R(0), sT = R(0);
-    if (mm > 0)
-#pragma unroll
-      for (int g = 0; g < GW; ++g) {
-        sF += red[cc][g][0][v * (NM - 1) + mm - 1];
-        sT += red[cc][g][1][v * (NM - 1) + mm - 1];
-      }
+    const size_t idx = (size_t)(v * NM + n) * nc + cell;
 #pragma unroll
     for (int D = 0; D < 3; ++D) {
-      const int t = tix[D * NM + mm];
-      const R sg = (R)tix[3 * NM + D * NM + mm];
+      const int t = tix[D * NM + n];
+      const R sg = (R)tix[3 * NM + D * NM + n];
       size_t up;
       if (D == 0)
         up = row + wrapm(i + 1, nx);
@@ -528,14 +528,11 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
         up = ((size_t)k * ny + wrapm(j + 1, ny)) * nx + i;
       else
         up = ((size_t)wrapm(k + 1, nz) * ny + j) * nx + i;
-      const R* gF = G + ((size_t)(D * 10 + v) * NT + t) * nc;
-      const R* gT = G + ((size_t)(D * 10 + 5 + v) * NT + t) * nc;
-      sF += sg * gF[cell] - gF[up];
-      sT += sg * gT[cell] - gT[up];
+      const R* gD = G + (size_t)D * nc * (10 * NT) + v * NT + t;  // face-major: [D][face][10][NT]
+      sF += sg * gD[cell * (10 * NT)] - gD[up * (10 * NT)];
+      sT += sg * gD[cell * (10 * NT) + 5 * NT] - gD[up * (10 * NT) + 5 * NT];
     }
-    // M^-1 and the stage increments in the flux precision R; the
-    // accumulation into the stored FP64 state is the one FP64 operation.
-    R iM = (R)invM[mm];
+    R iM = invM[n];
     if (mesh_nonuniform(m))  // 1/|K| = (2/h_x)(2/h_y)(2/h_z) / 8
       iM *= cell_sc<R>(m, 0, i) * cell_sc<R>(m, 1, j) * cell_sc<R>(m, 2, k) * R(0.125);
     const R Lv = sF * iM, Ltv = sT * iM;
@@ -543,12 +540,75 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
       io.L[idx] = (double)Lv;
       io.Lt[idx] = (double)Ltv;
     } else if (MODE == MODE_STAGE1) {
-      const R h = (R)dt, h2 = (R)(dt * dt);
-      io.Qs[idx] = coef[v * NM + mm][cc] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
+      io.Qs[idx] = coef[v * NM + n][cc] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
       io.inc[idx] = h * Lv + (h2 * R(1.0 / 6.0)) * Ltv;
     } else {
-      const R h2 = (R)(dt * dt);
       io.Qn[idx] = io.Qn[idx] + (double)(io.inc[idx] + (h2 * R(1.0 / 3.0)) * Ltv);
+    }
+  };
+  // this lane's contribution to output o (v = o / NM, mode n = o % NM; mode 0 has no volume term)
+  auto vol_term = [&](const R(&Fk)[3][5], int o) {
+    R c = R(0);
+    if (o < 5 * NM) {
+      const int v = o / NM, n = o % NM;
+      const int e0 = mode_exp(n, 0), e1 = mode_exp(n, 1), e2 = mode_exp(n, 2);
+      if (e0 > 0) c += Fk[0][v] * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
+      if (e1 > 0) c += Fk[1][v] * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
+      if (e2 > 0) c += Fk[2][v] * (L1[0][e0] * L1[1][e1] * dL1[2][e2]);
+    }
+    return c;
+  };
+
+  if constexpr (GW == 1) {
+    // ---- volume projection fused with the epilogue: the PG lanes of a cell
+    // reduce PG outputs at a time by a butterfly, after which lane lg holds
+    // output c0 + lg of both kinds (F and F_t) and finishes it.  No
+    // cross-warp exchange, no second barrier. ----
+    constexpr int NO = 5 * NM, NOP1 = (NO + PG - 1) / PG * PG;
+#pragma unroll
+    for (int c0 = 0; c0 < NOP1; c0 += PG) {
+      R vF[PG], vT[PG];
+#pragma unroll
+      for (int oo = 0; oo < PG; ++oo) {
+        vF[oo] = vol_term(Fw, c0 + oo);
+        vT[oo] = vol_term(Ftw, c0 + oo);
+      }
+      R oF[1], oT[1];
+      group_reduce<PG, PG>(vF, oF, lg);
+      group_reduce<PG, PG>(vT, oT, lg);
+      const int o = c0 + lg;
+      if (o < NO && i0 + cb < nx) finish(o / NM, o % NM, i0 + cb, cb, oF[0], oT[0]);
+    }
+  } else {
+    // ---- a cell spans GW warps: per-warp butterflies over the modes n >= 1,
+    // partial sums through shared memory, then the epilogue over the CTA ----
+#pragma unroll
+    for (int kind = 0; kind < 2; ++kind) {
+#pragma unroll
+      for (int c0 = 0; c0 < NOP; c0 += PG) {
+        R val[PG];
+#pragma unroll
+        for (int oo = 0; oo < PG; ++oo) {
+          const int o = c0 + oo;  // v = o / (NM - 1), n = 1 + o % (NM - 1)
+          val[oo] = o < NOUT ? vol_term(kind == 0 ? Fw : Ftw, (o / (NM - 1)) * NM + 1 + o % (NM - 1)) : R(0);
+        }
+        R outv[1];
+        group_reduce<PG, PG>(val, outv, lg);
+        red[cb][gw][kind][c0 + lg] = outv[0];
+      }
+    }
+    __syncthreads();
+    for (int o = tid; o < CB * NC; o += nthr) {
+      const int cc = o % CB, rest = o / CB, mm = rest % NM, v = rest / NM;
+      if (i0 + cc >= nx) continue;
+      R sF = R(0), sT = R(0);
+      if (mm > 0)
+#pragma unroll
+        for (int g = 0; g < GW; ++g) {
+          sF += red[cc][g][0][v * (NM - 1) + mm - 1];
+          sT += red[cc][g][1][v * (NM - 1) + mm - 1];
+        }
+      finish(v, mm, i0 + cc, cc, sF, sT);
     }
   }
 }

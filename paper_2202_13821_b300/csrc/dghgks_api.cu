@@ -38,7 +38,7 @@ struct dghgks_ctx {
   double gamma = 1.4, K = 2.0, mu = 0, Pr = 1, tau_eps = 0;
   void* Qs = nullptr;   // Q* (stage-1 output), flux precision
   void* Inc = nullptr;  // dt L + dt^2/6 L_t (stage-1 output), flux precision
-  void* G = nullptr;      // face moments [3][10][NT][cells], flux precision
+  void* G = nullptr;      // face moments [3][cells][10][NT] (face-major), flux precision
   unsigned* flag = nullptr;
   double* part = nullptr;  // reduction partials [kRedBlocks][5]
   double* red = nullptr;   // reduction results (device)
@@ -109,6 +109,8 @@ MeshDev mesh_dev(const dghgks_ctx* c) {
   }
   m.vol = c->vol;
   m.vol_f = (float)c->vol;
+  m.ivol = 1.0 / c->vol;
+  m.ivol_f = (float)(1.0 / c->vol);
   int off = 0;
   for (int d = 0; d < 3; ++d) {
     m.geo64[d] = c->nonuniform ? c->geo64 + off : nullptr;
@@ -137,7 +139,8 @@ struct ProfScope {
 
 struct Ops {
   cudaError_t (*set_attrs)();
-  // face pass on a state stored in FP64 (q_in_r = false) or in the flux precision
+  // face pass on a state stored in FP64 (q_in_r = false), or the stage-2 pass on
+  // Q* stored in the flux precision (q_in_r = true; F_t moments only)
   void (*faces)(dghgks_ctx*, const void*, bool, double, cudaStream_t);
   // cell pass: MODE_RESIDUAL (Q, L, Lt), MODE_STAGE1 (Q^n), MODE_STAGE2 (Q^n updated in place)
   void (*cell)(dghgks_ctx*, int, double*, double*, double*, double, cudaStream_t);
@@ -158,9 +161,9 @@ struct Impl {
     DG_ATTR((k_face<R, ORDER, NQ, 0, double>), FS::bytes)
     DG_ATTR((k_face<R, ORDER, NQ, 1, double>), FS::bytes)
     DG_ATTR((k_face<R, ORDER, NQ, 2, double>), FS::bytes)
-    DG_ATTR((k_face<R, ORDER, NQ, 0, R>), FS::bytes)
-    DG_ATTR((k_face<R, ORDER, NQ, 1, R>), FS::bytes)
-    DG_ATTR((k_face<R, ORDER, NQ, 2, R>), FS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 0, R, true>), FS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 1, R, true>), FS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 2, R, true>), FS::bytes)
     DG_ATTR((k_cell<R, ORDER, NQ, MODE_RESIDUAL, double>), CS::bytes)
     DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, double>), CS::bytes)
     DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE2, R>), CS::bytes)
@@ -168,7 +171,7 @@ struct Impl {
     return e;
   }
 
-  template <class Tin>
+  template <class Tin, bool FTO>
   static void faces_t(dghgks_ctx* c, const Tin* Q, double dt, cudaStream_t s) {
     const GasPar<R> g = gas_par<R>(c, dt);
     const MeshDev m = mesh_dev(c);
@@ -177,24 +180,24 @@ struct Impl {
     R* G = static_cast<R*>(c->G);
     {
       ProfScope ps(c, 0, s);
-      k_face<R, ORDER, NQ, 0, Tin><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
+      k_face<R, ORDER, NQ, 0, Tin, FTO><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
     }
     {
       ProfScope ps(c, 1, s);
-      k_face<R, ORDER, NQ, 1, Tin><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
+      k_face<R, ORDER, NQ, 1, Tin, FTO><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
     }
     {
       ProfScope ps(c, 2, s);
-      k_face<R, ORDER, NQ, 2, Tin><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
+      k_face<R, ORDER, NQ, 2, Tin, FTO><<<grid, block, FS::bytes, s>>>(Q, G, g, m, c->flag);
     }
     c->launches += 3;
   }
 
   static void faces(dghgks_ctx* c, const void* Q, bool q_in_r, double dt, cudaStream_t s) {
-    if (q_in_r)
-      faces_t<R>(c, static_cast<const R*>(Q), dt, s);
+    if (q_in_r)  // the stage-2 pass on Q*: F_t moments only
+      faces_t<R, true>(c, static_cast<const R*>(Q), dt, s);
     else
-      faces_t<double>(c, static_cast<const double*>(Q), dt, s);
+      faces_t<double, false>(c, static_cast<const double*>(Q), dt, s);
   }
 
   static void cell(dghgks_ctx* c, int mode, double* Q, double* L, double* Lt, double dt, cudaStream_t s) {

@@ -160,6 +160,8 @@ extern "C" int dghgks_residual_static(const dghgks_mesh* mesh, int order, double
     m.area_f[k] = (float)(m.vol / m.h[k]);
   }
   m.vol_f = (float)m.vol;
+  m.ivol = 1.0 / m.vol;
+  m.ivol_f = (float)(1.0 / m.vol);
   for (int k = 0; k < 3; ++k) {
     m.geo64[k] = nullptr;
     m.geo32[k] = nullptr;
