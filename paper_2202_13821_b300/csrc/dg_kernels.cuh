@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   SideSums<R> sums;
   iface_zero(sums);
   bool ok = true;
-#pragma unroll
+#pragma unroll 1  // sides in turn, not interleaved: fewer live registers
   for (int side = 0; side < 2; ++side) {
     R q[5], dq[3][5];  // global axes
 #pragma unroll
@@ -275,10 +275,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
       dql[ii][3] = src[1 + A2];
       dql[ii][4] = src[4];
     }
-    if (side == 0)
-      ok = iface_side<R, +1>(ql, dql, gp, pr_fix, sums) && ok;
-    else
-      ok = iface_side<R, -1>(ql, dql, gp, pr_fix, sums) && ok;
+    ok = iface_side<R>(side == 0 ? 1 : -1, ql, dql, gp, pr_fix, sums) && ok;
   }
   R Fl[5], Ftl[5];
   ok = iface_finish(sums, gp, Fl, Ftl) && ok;
@@ -413,12 +410,17 @@ struct StageIO {
 };
 
 // Resident CTAs of k_cell per SM requested from the compiler (FP32): 2 gives
-// the register cap 128.
+// the register cap 128; the stage-2 pass (L_t only) fits 3 (cap 80) without
+// spills for n_q <= 3.
 #ifndef CELL_MIN_CTAS_F32
 #define CELL_MIN_CTAS_F32 2
 #endif
+template <class R, int NQ, int MODE>
+constexpr int cell_min_ctas() {
+  return sizeof(R) == 4 ? (MODE == 2 && NQ <= 3 ? 3 : CELL_MIN_CTAS_F32) : 1;
+}
 template <class R, int ORDER, int NQ, int MODE, class Tin>
-__global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) == 4 ? CELL_MIN_CTAS_F32 : 1)
+__global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_ctas<R, NQ, MODE>()))
     k_cell(const Tin* __restrict__ Qin, const R* __restrict__ G, const StageIO<R> io, const GasPar<R> gp,
            const MeshDev m, const double dt, unsigned* __restrict__ flag) {
   using LY = CellLayout<ORDER, NQ>;
@@ -428,11 +430,10 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, sizeof(R) =
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R(*coef)[CB] = reinterpret_cast<R(*)[CB]>(smem_raw);
   R(*red)[GW][2][NOP] = reinterpret_cast<R(*)[GW][2][NOP]>(smem_raw + S::coef);  // GW > 1 only
-  R* invM = reinterpret_cast<R*>(smem_raw + S::coef + S::red);
-  int* tix = reinterpret_cast<int*>(invM + NM);  // [3][NM] tangential index, then [3][NM] parity sign
-
   const int tid = threadIdx.x, nthr = LY::WARPS * 32;
   const int lane = tid & 31, lg = lane % PG, warp = tid >> 5;
+  R* invM = reinterpret_cast<R*>(smem_raw + S::coef + S::red);
+  int* tix = reinterpret_cast<int*>(invM + NM);  // [3][NM] tangential index, then [3][NM] parity sign
   const int cb = GW == 1 ? warp * LY::CPW + lane / PG : warp / GW;  // cell of this lane within the CTA
   const int gw = GW == 1 ? 0 : warp % GW;                            // which warp of the cell
   const int pidx = gw * 32 + lg;                                      // Gauss point of this lane

@@ -107,13 +107,9 @@ DG_HD void half_line(R* m, R U, R lam, R h, int sgn) {
   const R rs = frsqrt(lam);
   const R sl = lam * rs;  // sqrt(lam)
   const R e = fexp(-lam * U * U) * (R(0.28209479177387814347) * rs);  // exp(-lam U^2) / (2 sqrt(pi lam))
-  if (sgn > 0) {
-    m[0] = R(0.5) * erfc(-sl * U);
-    m[1] = U * m[0] + e;
-  } else {
-    m[0] = R(0.5) * erfc(sl * U);
-    m[1] = U * m[0] - e;
-  }
+  const R sg = sgn > 0 ? R(1) : R(-1);  // u > 0 (sgn = +1) or u < 0 half space
+  m[0] = R(0.5) * erfc(-sg * sl * U);
+  m[1] = U * m[0] + sg * e;
   raw_moments_tail(m, U, h);
 }
 
@@ -278,9 +274,12 @@ struct SideSums {
   R W5[5], W6[5];         // density moments of terms 5 and 6 (Prandtl fix only)
 };
 
-template <class R, int SGN>
-DG_HD bool iface_side(const R q[5], const R dq[3][5], const GasPar<R>& g, bool pr_fix,
-                                           SideSums<R>& S) {
+// One side of the interface: SGN = +1 for the left state (its u > 0
+// half-space reaches the interface), -1 for the right state.  SGN is a runtime
+// value so that a kernel can loop over the two sides without unrolling.
+template <class R>
+DG_HD bool iface_side(int SGN, const R q[5], const R dq[3][5], const GasPar<R>& g, bool pr_fix,
+                      SideSums<R>& S) {
   Prim<R> p;
   const bool ok = prim_of(q, g.gm1, p);
   const R ir = fdiv(R(1), p.rho);
@@ -313,6 +312,11 @@ DG_HD bool iface_side(const R q[5], const R dq[3][5], const GasPar<R>& g, bool p
     mom_a_psi<0, 0, 0>(t, A, r, S.W6);
   }
   return ok;
+}
+
+template <class R, int SGN>
+DG_HD bool iface_side(const R q[5], const R dq[3][5], const GasPar<R>& g, bool pr_fix, SideSums<R>& S) {
+  return iface_side<R>(SGN, q, dq, g, pr_fix, S);
 }
 
 template <class R>
