@@ -40,6 +40,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "dg_tables.cuh"
 #include "gks_point.cuh"
 
@@ -352,15 +354,20 @@ struct CellLayout {
   static_assert(NP <= 64, "k_cell handles up to 4^3 points per cell");
 };
 
-template <class R, int ORDER, int NQ>
+template <class R, int ORDER, int NQ, class Tin = R>
 struct CellSmem {
   using LY = CellLayout<ORDER, NQ>;
   static constexpr int NM = LY::NM, NC = 5 * NM, CB = LY::CB;
-  static constexpr size_t coef = sizeof(R) * NC * CB;
+  // GW = 1: two staging buffers of the input type (cp.async targets), plus a
+  // converted copy when the input is not in the flux precision; GW > 1: one
+  // buffer in the flux precision.
+  static constexpr size_t raw = LY::GW == 1 ? 2 * sizeof(Tin) * NC * CB : 0;
+  static constexpr size_t cvt = (LY::GW == 1 && std::is_same<Tin, R>::value) ? 0 : sizeof(R) * NC * CB;
   // cross-warp partial sums (only when a cell spans two warps)
   static constexpr size_t red = LY::GW == 1 ? 0 : sizeof(R) * CB * LY::GW * 2 * LY::NOP;
   static constexpr size_t tabs = sizeof(R) * NM + sizeof(int) * 6 * NM;
-  static constexpr size_t bytes = coef + red + tabs;
+  static constexpr size_t cvt_off = raw, red_off = raw + cvt, tab_off = raw + cvt + red;
+  static constexpr size_t bytes = raw + cvt + red + tabs;
 };
 
 // Recursive-halving butterfly over the PG lanes of a group: in[N] per lane ->
@@ -395,6 +402,19 @@ __device__ __forceinline__ void group_reduce(const R (&val)[NOP], R (&out)[NOP /
   }
 }
 
+// cp.async (global -> shared, 4 or 8 bytes, bypassing registers); zfill:
+// with valid = false nothing is read and the destination is zeroed.
+template <class T>
+__device__ __forceinline__ void cp_async_zfill(T* smem, const T* gmem, bool valid) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? (int)sizeof(T) : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gmem), "n"(sizeof(T)), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Buffers of the cell-kernel epilogue.
 //   MODE 0: L, Lt (FP64, caller's)
 //   MODE 1: Qs = Q* and inc = dt L + dt^2/6 L_t, both in the flux precision R
@@ -424,28 +444,21 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     k_cell(const Tin* __restrict__ Qin, const R* __restrict__ G, const StageIO<R> io, const GasPar<R> gp,
            const MeshDev m, const double dt, unsigned* __restrict__ flag) {
   using LY = CellLayout<ORDER, NQ>;
-  using S = CellSmem<R, ORDER, NQ>;
+  using S = CellSmem<R, ORDER, NQ, Tin>;
   constexpr int NM = LY::NM, NP = LY::NP, NC = S::NC, CB = LY::CB, PG = LY::PG, GW = LY::GW, NT = n_tmodes(ORDER);
   constexpr int NOUT = LY::NOUT, NOP = LY::NOP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R(*coef)[CB] = reinterpret_cast<R(*)[CB]>(smem_raw);
-  R(*red)[GW][2][NOP] = reinterpret_cast<R(*)[GW][2][NOP]>(smem_raw + S::coef);  // GW > 1 only
+  R(*red)[GW][2][NOP] = reinterpret_cast<R(*)[GW][2][NOP]>(smem_raw + S::red_off);  // GW > 1 only
+  R* invM = reinterpret_cast<R*>(smem_raw + S::tab_off);
+  int* tix = reinterpret_cast<int*>(invM + NM);  // [3][NM] tangential index, then [3][NM] parity sign
   const int tid = threadIdx.x, nthr = LY::WARPS * 32;
   const int lane = tid & 31, lg = lane % PG, warp = tid >> 5;
-  R* invM = reinterpret_cast<R*>(smem_raw + S::coef + S::red);
-  int* tix = reinterpret_cast<int*>(invM + NM);  // [3][NM] tangential index, then [3][NM] parity sign
   const int cb = GW == 1 ? warp * LY::CPW + lane / PG : warp / GW;  // cell of this lane within the CTA
   const int gw = GW == 1 ? 0 : warp % GW;                            // which warp of the cell
   const int pidx = gw * 32 + lg;                                      // Gauss point of this lane
-  const int i0 = blockIdx.x * CB, j = blockIdx.y, k = blockIdx.z;
   const int nx = m.nx, ny = m.ny, nz = m.nz;
   const long long nc = m.ncell;
-  const size_t row = ((size_t)k * ny + j) * nx;
 
-  for (int e = tid; e < NC * CB; e += nthr) {
-    const int cc = e % CB, comp = e / CB, i = i0 + cc;
-    coef[comp][cc] = (i < nx) ? (R)__ldg(Qin + (size_t)comp * nc + row + i) : R(0);
-  }
   for (int e = tid; e < NM; e += nthr) {
     // (2a+1)(2b+1)(2c+1) / |K|; on a rectilinear mesh the 1/|K| of each cell
     // is applied in the epilogue
@@ -457,161 +470,243 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       tix[3 * NM + D * NM + e] = (mode_exp(e, D) % 2 == 0) ? 1 : -1;
     }
   }
-  __syncthreads();
 
-  // ---- interior flux of Eq. (flux-2) at this lane's Gauss point ----
-  const bool active = (pidx < NP) && (i0 + cb < nx);
-  const int pp = active ? pidx : 0;
-  const int pa[3] = {pp / (NQ * NQ), (pp / NQ) % NQ, pp % NQ};
-  R L1[3][ORDER + 1], dL1[3][ORDER + 1];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const R x = gauss_xr<R>(NQ, pa[d]);
-#pragma unroll
-    for (int n = 0; n <= ORDER; ++n) {
-      L1[d][n] = leg<R>(n, x);
-      dL1[d][n] = dleg<R>(n, x);
-    }
-  }
-  const int icell = (i0 + cb < nx) ? i0 + cb : nx - 1;
-  const R sc[3] = {cell_sc<R>(m, 0, icell), cell_sc<R>(m, 1, j), cell_sc<R>(m, 2, k)};
-  const R cvol = mesh_nonuniform(m) ? cell_w<R>(m, 0, icell) * cell_w<R>(m, 1, j) * cell_w<R>(m, 2, k) : mesh_vol<R>(m);
-  R Fw[3][5], Ftw[3][5];  // w |K| (2/h_d) F_d, same for F_t
-  {
-    R q[5], dq[3][5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      R s0 = R(0), g0 = R(0), g1 = R(0), g2 = R(0);
-#pragma unroll
-      for (int mm = 0; mm < NM; ++mm) {
-        const int e0 = mode_exp(mm, 0), e1 = mode_exp(mm, 1), e2 = mode_exp(mm, 2);
-        const R cv = coef[v * NM + mm][cb];
-        s0 += cv * (L1[0][e0] * L1[1][e1] * L1[2][e2]);
-        g0 += cv * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
-        g1 += cv * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
-        g2 += cv * (L1[0][e0] * L1[1][e1] * dL1[2][e2]);
+  // Everything after the staging of one tile (CB consecutive cells along x of
+  // row (j, k)), reading the coefficients from coef[NC][CB].
+  auto tile = [&](const int i0, const int j, const int k, const R (*coef)[CB]) {
+    const size_t row = ((size_t)k * ny + j) * nx;
+    // ---- interior flux of Eq. (flux-2) at this lane's Gauss point ----
+    const bool active = (pidx < NP) && (i0 + cb < nx);
+    const int pp = active ? pidx : 0;
+    const int pa[3] = {pp / (NQ * NQ), (pp / NQ) % NQ, pp % NQ};
+    R L1[3][ORDER + 1], dL1[3][ORDER + 1];
+  #pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const R x = gauss_xr<R>(NQ, pa[d]);
+  #pragma unroll
+      for (int n = 0; n <= ORDER; ++n) {
+        L1[d][n] = leg<R>(n, x);
+        dL1[d][n] = dleg<R>(n, x);
       }
-      q[v] = s0;
-      dq[0][v] = g0 * sc[0];
-      dq[1][v] = g1 * sc[1];
-      dq[2][v] = g2 * sc[2];
     }
-    R F[3][5], Ft[3][5];
-    bool ok = true;
-    if (active) ok = interior_flux(q, dq, gp, F, Ft);
-    if (active && !ok) atomicOr(flag, 1u);
-    const R w = active ? gauss_wr<R>(NQ, pa[0]) * gauss_wr<R>(NQ, pa[1]) * gauss_wr<R>(NQ, pa[2]) * cvol : R(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
+    const int icell = (i0 + cb < nx) ? i0 + cb : nx - 1;
+    const R sc[3] = {cell_sc<R>(m, 0, icell), cell_sc<R>(m, 1, j), cell_sc<R>(m, 2, k)};
+    const R cvol = mesh_nonuniform(m) ? cell_w<R>(m, 0, icell) * cell_w<R>(m, 1, j) * cell_w<R>(m, 2, k) : mesh_vol<R>(m);
+    R Fw[3][5], Ftw[3][5];  // w |K| (2/h_d) F_d, same for F_t
+    {
+      R q[5], dq[3][5];
+  #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        Fw[d][v] = active ? w * sc[d] * F[d][v] : R(0);
-        Ftw[d][v] = active ? w * sc[d] * Ft[d][v] : R(0);
+        R s0 = R(0), g0 = R(0), g1 = R(0), g2 = R(0);
+  #pragma unroll
+        for (int mm = 0; mm < NM; ++mm) {
+          const int e0 = mode_exp(mm, 0), e1 = mode_exp(mm, 1), e2 = mode_exp(mm, 2);
+          const R cv = coef[v * NM + mm][cb];
+          s0 += cv * (L1[0][e0] * L1[1][e1] * L1[2][e2]);
+          g0 += cv * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
+          g1 += cv * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
+          g2 += cv * (L1[0][e0] * L1[1][e1] * dL1[2][e2]);
+        }
+        q[v] = s0;
+        dq[0][v] = g0 * sc[0];
+        dq[1][v] = g1 * sc[1];
+        dq[2][v] = g2 * sc[2];
       }
-  }
+      R F[3][5], Ft[3][5];
+      bool ok = true;
+      if (active) ok = interior_flux(q, dq, gp, F, Ft);
+      if (active && !ok) atomicOr(flag, 1u);
+      const R w = active ? gauss_wr<R>(NQ, pa[0]) * gauss_wr<R>(NQ, pa[1]) * gauss_wr<R>(NQ, pa[2]) * cvol : R(0);
+  #pragma unroll
+      for (int d = 0; d < 3; ++d)
+  #pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          Fw[d][v] = active ? w * sc[d] * F[d][v] : R(0);
+          Ftw[d][v] = active ? w * sc[d] * Ft[d][v] : R(0);
+        }
+    }
 
-  // One output (variable v, mode n) of the cell at x index i: the six faces'
-  // moments with the sign/parity of Eq. (operator), M^-1, and the stage
-  // epilogue in the flux precision R; the accumulation into the stored FP64
-  // state is the one FP64 operation.
-  const R h = (R)dt, h2 = (R)(dt * dt);
-  auto finish = [&](int v, int n, int i, int cc, R sF, R sT) {
-    const size_t cell = row + i;
-    const size_t idx = (size_t)(v * NM + n) * nc + cell;
-#pragma unroll
-    for (int D = 0; D < 3; ++D) {
-      const int t = tix[D * NM + n];
-      const R sg = (R)tix[3 * NM + D * NM + n];
-      size_t up;
-      if (D == 0)
-        up = row + wrapm(i + 1, nx);
-      else if (D == 1)
-        up = ((size_t)k * ny + wrapm(j + 1, ny)) * nx + i;
-      else
-        up = ((size_t)wrapm(k + 1, nz) * ny + j) * nx + i;
-      const R* gD = G + (size_t)D * nc * (10 * NT) + v * NT + t;  // face-major: [D][face][10][NT]
-      sF += sg * gD[cell * (10 * NT)] - gD[up * (10 * NT)];
-      sT += sg * gD[cell * (10 * NT) + 5 * NT] - gD[up * (10 * NT) + 5 * NT];
-    }
-    R iM = invM[n];
-    if (mesh_nonuniform(m))  // 1/|K| = (2/h_x)(2/h_y)(2/h_z) / 8
-      iM *= cell_sc<R>(m, 0, i) * cell_sc<R>(m, 1, j) * cell_sc<R>(m, 2, k) * R(0.125);
-    const R Lv = sF * iM, Ltv = sT * iM;
-    if (MODE == MODE_RESIDUAL) {
-      io.L[idx] = (double)Lv;
-      io.Lt[idx] = (double)Ltv;
-    } else if (MODE == MODE_STAGE1) {
-      io.Qs[idx] = coef[v * NM + n][cc] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
-      io.inc[idx] = h * Lv + (h2 * R(1.0 / 6.0)) * Ltv;
+    // One output (variable v, mode n) of the cell at x index i: the six faces'
+    // moments with the sign/parity of Eq. (operator), M^-1, and the stage
+    // epilogue in the flux precision R; the accumulation into the stored FP64
+    // state is the one FP64 operation.
+    const R h = (R)dt, h2 = (R)(dt * dt);
+    auto finish = [&](int v, int n, int i, int cc, R sF, R sT) {
+      const size_t cell = row + i;
+      const size_t idx = (size_t)(v * NM + n) * nc + cell;
+  #pragma unroll
+      for (int D = 0; D < 3; ++D) {
+        const int t = tix[D * NM + n];
+        const R sg = (R)tix[3 * NM + D * NM + n];
+        size_t up;
+        if (D == 0)
+          up = row + wrapm(i + 1, nx);
+        else if (D == 1)
+          up = ((size_t)k * ny + wrapm(j + 1, ny)) * nx + i;
+        else
+          up = ((size_t)wrapm(k + 1, nz) * ny + j) * nx + i;
+        const R* gD = G + (size_t)D * nc * (10 * NT) + v * NT + t;  // face-major: [D][face][10][NT]
+        sF += sg * gD[cell * (10 * NT)] - gD[up * (10 * NT)];
+        sT += sg * gD[cell * (10 * NT) + 5 * NT] - gD[up * (10 * NT) + 5 * NT];
+      }
+      R iM = invM[n];
+      if (mesh_nonuniform(m))  // 1/|K| = (2/h_x)(2/h_y)(2/h_z) / 8
+        iM *= cell_sc<R>(m, 0, i) * cell_sc<R>(m, 1, j) * cell_sc<R>(m, 2, k) * R(0.125);
+      const R Lv = sF * iM, Ltv = sT * iM;
+      if (MODE == MODE_RESIDUAL) {
+        io.L[idx] = (double)Lv;
+        io.Lt[idx] = (double)Ltv;
+      } else if (MODE == MODE_STAGE1) {
+        io.Qs[idx] = coef[v * NM + n][cc] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
+        io.inc[idx] = h * Lv + (h2 * R(1.0 / 6.0)) * Ltv;
+      } else {
+        io.Qn[idx] = io.Qn[idx] + (double)(io.inc[idx] + (h2 * R(1.0 / 3.0)) * Ltv);
+      }
+    };
+    // this lane's contribution to output o (v = o / NM, mode n = o % NM; mode 0 has no volume term)
+    auto vol_term = [&](const R(&Fk)[3][5], int o) {
+      R c = R(0);
+      if (o < 5 * NM) {
+        const int v = o / NM, n = o % NM;
+        const int e0 = mode_exp(n, 0), e1 = mode_exp(n, 1), e2 = mode_exp(n, 2);
+        if (e0 > 0) c += Fk[0][v] * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
+        if (e1 > 0) c += Fk[1][v] * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
+        if (e2 > 0) c += Fk[2][v] * (L1[0][e0] * L1[1][e1] * dL1[2][e2]);
+      }
+      return c;
+    };
+
+    if constexpr (GW == 1) {
+      // ---- volume projection fused with the epilogue: the PG lanes of a cell
+      // reduce PG outputs at a time by a butterfly, after which lane lg holds
+      // output c0 + lg of both kinds (F and F_t) and finishes it.  No
+      // cross-warp exchange, no second barrier. ----
+      constexpr int NO = 5 * NM, NOP1 = (NO + PG - 1) / PG * PG;
+  #pragma unroll
+      for (int c0 = 0; c0 < NOP1; c0 += PG) {
+        R vF[PG], vT[PG];
+  #pragma unroll
+        for (int oo = 0; oo < PG; ++oo) {
+          vF[oo] = vol_term(Fw, c0 + oo);
+          vT[oo] = vol_term(Ftw, c0 + oo);
+        }
+        R oF[1], oT[1];
+        group_reduce<PG, PG>(vF, oF, lg);
+        group_reduce<PG, PG>(vT, oT, lg);
+        const int o = c0 + lg;
+        if (o < NO && i0 + cb < nx) finish(o / NM, o % NM, i0 + cb, cb, oF[0], oT[0]);
+      }
     } else {
-      io.Qn[idx] = io.Qn[idx] + (double)(io.inc[idx] + (h2 * R(1.0 / 3.0)) * Ltv);
+      // ---- a cell spans GW warps: per-warp butterflies over the modes n >= 1,
+      // partial sums through shared memory, then the epilogue over the CTA ----
+  #pragma unroll
+      for (int kind = 0; kind < 2; ++kind) {
+  #pragma unroll
+        for (int c0 = 0; c0 < NOP; c0 += PG) {
+          R val[PG];
+  #pragma unroll
+          for (int oo = 0; oo < PG; ++oo) {
+            const int o = c0 + oo;  // v = o / (NM - 1), n = 1 + o % (NM - 1)
+            val[oo] = o < NOUT ? vol_term(kind == 0 ? Fw : Ftw, (o / (NM - 1)) * NM + 1 + o % (NM - 1)) : R(0);
+          }
+          R outv[1];
+          group_reduce<PG, PG>(val, outv, lg);
+          red[cb][gw][kind][c0 + lg] = outv[0];
+        }
+      }
+      __syncthreads();
+      for (int o = tid; o < CB * NC; o += nthr) {
+        const int cc = o % CB, rest = o / CB, mm = rest % NM, v = rest / NM;
+        if (i0 + cc >= nx) continue;
+        R sF = R(0), sT = R(0);
+        if (mm > 0)
+  #pragma unroll
+          for (int g = 0; g < GW; ++g) {
+            sF += red[cc][g][0][v * (NM - 1) + mm - 1];
+            sT += red[cc][g][1][v * (NM - 1) + mm - 1];
+          }
+        finish(v, mm, i0 + cc, cc, sF, sT);
+      }
     }
-  };
-  // this lane's contribution to output o (v = o / NM, mode n = o % NM; mode 0 has no volume term)
-  auto vol_term = [&](const R(&Fk)[3][5], int o) {
-    R c = R(0);
-    if (o < 5 * NM) {
-      const int v = o / NM, n = o % NM;
-      const int e0 = mode_exp(n, 0), e1 = mode_exp(n, 1), e2 = mode_exp(n, 2);
-      if (e0 > 0) c += Fk[0][v] * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
-      if (e1 > 0) c += Fk[1][v] * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
-      if (e2 > 0) c += Fk[2][v] * (L1[0][e0] * L1[1][e1] * dL1[2][e2]);
-    }
-    return c;
   };
 
   if constexpr (GW == 1) {
-    // ---- volume projection fused with the epilogue: the PG lanes of a cell
-    // reduce PG outputs at a time by a butterfly, after which lane lg holds
-    // output c0 + lg of both kinds (F and F_t) and finishes it.  No
-    // cross-warp exchange, no second barrier. ----
-    constexpr int NO = 5 * NM, NOP1 = (NO + PG - 1) / PG * PG;
-#pragma unroll
-    for (int c0 = 0; c0 < NOP1; c0 += PG) {
-      R vF[PG], vT[PG];
-#pragma unroll
-      for (int oo = 0; oo < PG; ++oo) {
-        vF[oo] = vol_term(Fw, c0 + oo);
-        vT[oo] = vol_term(Ftw, c0 + oo);
+    // Persistent CTAs over the tiles; the coefficients of the next tile are
+    // copied global -> shared with cp.async (double buffer) while the current
+    // tile is computed, so a CTA waits at its one barrier per tile only for
+    // the slowest of its warps, not for memory.
+    Tin(*raw)[NC][CB] = reinterpret_cast<Tin(*)[NC][CB]>(smem_raw);
+    R(*cvt)[CB] = reinterpret_cast<R(*)[CB]>(smem_raw + S::cvt_off);  // converted copy (Tin != R)
+    const int ntx = (nx + CB - 1) / CB;
+    const long long ntiles = (long long)ntx * ny * nz;
+    auto issue = [&](long long t, int b) {
+      const int i0 = (int)(t % ntx) * CB;
+      const long long r = t / ntx;
+      const size_t row = (size_t)r * nx;  // r = k ny + j
+      for (int e = tid; e < NC * CB; e += nthr) {
+        const int cc = e % CB, comp = e / CB, i = i0 + cc;
+        cp_async_zfill(&raw[b][comp][cc], Qin + (size_t)comp * nc + row + (i < nx ? i : 0), i < nx);
       }
-      R oF[1], oT[1];
-      group_reduce<PG, PG>(vF, oF, lg);
-      group_reduce<PG, PG>(vT, oT, lg);
-      const int o = c0 + lg;
-      if (o < NO && i0 + cb < nx) finish(o / NM, o % NM, i0 + cb, cb, oF[0], oT[0]);
+      cp_async_commit();
+    };
+    long long t = blockIdx.x;
+    if (t < ntiles) issue(t, 0);
+    for (int b = 0; t < ntiles; t += gridDim.x, b ^= 1) {
+      cp_async_wait_all();
+      __syncthreads();  // tile t staged by all threads; every warp is done with buffer b ^ 1
+      if (t + gridDim.x < ntiles) issue(t + gridDim.x, b ^ 1);
+      const R(*coef)[CB];
+      if constexpr (std::is_same<Tin, R>::value) {
+        coef = raw[b];
+      } else {
+        // each warp converts its own cells (the only ones it reads)
+        for (int e = lane; e < NC * LY::CPW; e += 32) {
+          const int cc = warp * LY::CPW + e % LY::CPW, comp = e / LY::CPW;
+          cvt[comp][cc] = (R)raw[b][comp][cc];
+        }
+        __syncwarp();
+        coef = cvt;
+      }
+      const int i0 = (int)(t % ntx) * CB;
+      const long long r = t / ntx;
+      tile(i0, (int)(r % ny), (int)(r / ny), coef);
     }
   } else {
-    // ---- a cell spans GW warps: per-warp butterflies over the modes n >= 1,
-    // partial sums through shared memory, then the epilogue over the CTA ----
-#pragma unroll
-    for (int kind = 0; kind < 2; ++kind) {
-#pragma unroll
-      for (int c0 = 0; c0 < NOP; c0 += PG) {
-        R val[PG];
-#pragma unroll
-        for (int oo = 0; oo < PG; ++oo) {
-          const int o = c0 + oo;  // v = o / (NM - 1), n = 1 + o % (NM - 1)
-          val[oo] = o < NOUT ? vol_term(kind == 0 ? Fw : Ftw, (o / (NM - 1)) * NM + 1 + o % (NM - 1)) : R(0);
-        }
-        R outv[1];
-        group_reduce<PG, PG>(val, outv, lg);
-        red[cb][gw][kind][c0 + lg] = outv[0];
-      }
+    R(*coef)[CB] = reinterpret_cast<R(*)[CB]>(smem_raw + S::cvt_off);
+    const int i0 = blockIdx.x * CB, j = blockIdx.y, k = blockIdx.z;
+    const size_t row = ((size_t)k * ny + j) * nx;
+    for (int e = tid; e < NC * CB; e += nthr) {
+      const int cc = e % CB, comp = e / CB, i = i0 + cc;
+      coef[comp][cc] = (i < nx) ? (R)__ldg(Qin + (size_t)comp * nc + row + i) : R(0);
     }
     __syncthreads();
-    for (int o = tid; o < CB * NC; o += nthr) {
-      const int cc = o % CB, rest = o / CB, mm = rest % NM, v = rest / NM;
-      if (i0 + cc >= nx) continue;
-      R sF = R(0), sT = R(0);
-      if (mm > 0)
-#pragma unroll
-        for (int g = 0; g < GW; ++g) {
-          sF += red[cc][g][0][v * (NM - 1) + mm - 1];
-          sT += red[cc][g][1][v * (NM - 1) + mm - 1];
-        }
-      finish(v, mm, i0 + cc, cc, sF, sT);
-    }
+    tile(i0, j, k, coef);
   }
+}
+
+// Launch geometry of k_cell: persistent CTAs (resident CTAs per SM x SMs, at
+// most one per tile) when a cell fits in one warp, otherwise one CTA per tile.
+// The persistent kernel strides over the tiles, so any grid size is correct;
+// if the occupancy query fails, one CTA per tile is launched.
+template <class R, int ORDER, int NQ, int MODE, class Tin>
+inline void cell_launch_config(const MeshDev& m, dim3& grid, size_t& smem) {
+  using LY = CellLayout<ORDER, NQ>;
+  smem = CellSmem<R, ORDER, NQ, Tin>::bytes;
+  const long long ntx = (m.nx + LY::CB - 1) / LY::CB;
+  if (LY::GW != 1) {
+    grid = dim3((unsigned)ntx, (unsigned)m.ny, (unsigned)m.nz);
+    return;
+  }
+  const long long ntiles = ntx * m.ny * m.nz;
+  long long g = ntiles < 0x7fffffffLL ? ntiles : 0x7fffffffLL;
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cell<R, ORDER, NQ, MODE, Tin>, LY::WARPS * 32, smem) ==
+          cudaSuccess &&
+      sms > 0 && per > 0 && (long long)sms * per < g)
+    g = (long long)sms * per;
+  grid = dim3((unsigned)g);
 }
 
 // ---------------------------------------------------------------------------

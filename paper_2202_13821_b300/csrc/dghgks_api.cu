@@ -152,7 +152,6 @@ struct Ops {
 template <class R, int ORDER, int NQ>
 struct Impl {
   using FS = FaceSmem<R, ORDER, NQ>;
-  using CS = CellSmem<R, ORDER, NQ>;
 
   static cudaError_t set_attrs() {
     cudaError_t e = cudaSuccess;
@@ -164,9 +163,9 @@ struct Impl {
     DG_ATTR((k_face<R, ORDER, NQ, 0, R, true>), FS::bytes)
     DG_ATTR((k_face<R, ORDER, NQ, 1, R, true>), FS::bytes)
     DG_ATTR((k_face<R, ORDER, NQ, 2, R, true>), FS::bytes)
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_RESIDUAL, double>), CS::bytes)
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, double>), CS::bytes)
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE2, R>), CS::bytes)
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_RESIDUAL, double>), (CellSmem<R, ORDER, NQ, double>::bytes))
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, double>), (CellSmem<R, ORDER, NQ, double>::bytes))
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE2, R>), (CellSmem<R, ORDER, NQ, R>::bytes))
 #undef DG_ATTR
     return e;
   }
@@ -200,12 +199,18 @@ struct Impl {
       faces_t<double, false>(c, static_cast<const double*>(Q), dt, s);
   }
 
+  template <int MODE, class Tin>
+  static void cell_t(dghgks_ctx* c, const Tin* Qin, const R* G, const StageIO<R>& io, const GasPar<R>& g,
+                     const MeshDev& m, double dt, cudaStream_t s) {
+    dim3 grid;
+    size_t smem = 0;
+    cell_launch_config<R, ORDER, NQ, MODE, Tin>(m, grid, smem);
+    k_cell<R, ORDER, NQ, MODE, Tin><<<grid, CellLayout<ORDER, NQ>::WARPS * 32, smem, s>>>(Qin, G, io, g, m, dt, c->flag);
+  }
+
   static void cell(dghgks_ctx* c, int mode, double* Q, double* L, double* Lt, double dt, cudaStream_t s) {
     const GasPar<R> g = gas_par<R>(c, dt);
     const MeshDev m = mesh_dev(c);
-    using LY = CellLayout<ORDER, NQ>;
-    dim3 grid((c->n[0] + LY::CB - 1) / LY::CB, c->n[1], c->n[2]);
-    dim3 block(LY::WARPS * 32);
     const R* G = static_cast<const R*>(c->G);
     StageIO<R> io;
     io.L = L;
@@ -215,11 +220,11 @@ struct Impl {
     io.Qn = Q;
     ProfScope ps(c, 3 + mode, s);
     if (mode == MODE_RESIDUAL)
-      k_cell<R, ORDER, NQ, MODE_RESIDUAL, double><<<grid, block, CS::bytes, s>>>(Q, G, io, g, m, dt, c->flag);
+      cell_t<MODE_RESIDUAL, double>(c, Q, G, io, g, m, dt, s);
     else if (mode == MODE_STAGE1)
-      k_cell<R, ORDER, NQ, MODE_STAGE1, double><<<grid, block, CS::bytes, s>>>(Q, G, io, g, m, dt, c->flag);
+      cell_t<MODE_STAGE1, double>(c, Q, G, io, g, m, dt, s);
     else
-      k_cell<R, ORDER, NQ, MODE_STAGE2, R><<<grid, block, CS::bytes, s>>>(io.Qs, G, io, g, m, dt, c->flag);
+      cell_t<MODE_STAGE2, R>(c, io.Qs, G, io, g, m, dt, s);
     c->launches += 1;
   }
 

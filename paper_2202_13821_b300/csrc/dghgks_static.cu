@@ -44,13 +44,13 @@ std::mutex g_dev_mu;
 template <class R, int ORDER, int NQ>
 cudaError_t set_attrs() {
   using FS = FaceSmem<R, ORDER, NQ>;
-  using CS = CellSmem<R, ORDER, NQ>;
   cudaError_t e = cudaSuccess;
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face<R, ORDER, NQ, 0, double>, a, (int)FS::bytes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face<R, ORDER, NQ, 1, double>, a, (int)FS::bytes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face<R, ORDER, NQ, 2, double>, a, (int)FS::bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cell<R, ORDER, NQ, MODE_RESIDUAL, double>, a, (int)CS::bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cell<R, ORDER, NQ, MODE_RESIDUAL, double>, a, (int)CellSmem<R, ORDER, NQ, double>::bytes);
   return e;
 }
 
@@ -85,7 +85,6 @@ template <class R, int ORDER, int NQ>
 void launch(const MeshDev& m, const GasPar<R>& g, const double* Q, double* L, double* Lt, R* G, unsigned* flag,
             double dt, cudaStream_t s) {
   using FS = FaceSmem<R, ORDER, NQ>;
-  using CS = CellSmem<R, ORDER, NQ>;
   using LY = CellLayout<ORDER, NQ>;
   const dim3 fgrid((m.nx + FB - 1) / FB, m.ny, m.nz), fblock(FB * NQ * NQ);
   k_face<R, ORDER, NQ, 0, double><<<fgrid, fblock, FS::bytes, s>>>(Q, G, g, m, flag);
@@ -97,8 +96,10 @@ void launch(const MeshDev& m, const GasPar<R>& g, const double* Q, double* L, do
   io.Qs = nullptr;
   io.inc = nullptr;
   io.Qn = nullptr;
-  const dim3 cgrid((m.nx + LY::CB - 1) / LY::CB, m.ny, m.nz), cblock(LY::WARPS * 32);
-  k_cell<R, ORDER, NQ, MODE_RESIDUAL, double><<<cgrid, cblock, CS::bytes, s>>>(Q, G, io, g, m, dt, flag);
+  dim3 cgrid;
+  size_t csmem = 0;
+  cell_launch_config<R, ORDER, NQ, MODE_RESIDUAL, double>(m, cgrid, csmem);
+  k_cell<R, ORDER, NQ, MODE_RESIDUAL, double><<<cgrid, LY::WARPS * 32, csmem, s>>>(Q, G, io, g, m, dt, flag);
 }
 
 template <class R>
