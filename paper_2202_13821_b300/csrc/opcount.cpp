@@ -17,8 +17,10 @@
 #include <cmath>
 #include <cstdio>
 #include <map>
+#include <set>
 #include <tuple>
 #include <utility>
+#include <vector>
 
 namespace opc {
 // Value numbering: every distinct (operation, operands) pair is counted once,
@@ -30,6 +32,7 @@ struct Tally {
 };
 Tally g;
 std::map<std::tuple<char, int, int>, int> memo;
+std::map<int, std::tuple<char, int, int>> nodes;  // the operation that produced each id
 std::map<double, int> const_ids;
 std::map<int, double> const_vals;
 int next_id = 1;
@@ -49,6 +52,7 @@ inline bool is_const(int id, double x) {
 inline void reset() {
   g = Tally();
   memo.clear();
+  nodes.clear();
 }
 
 struct Cnt {
@@ -69,7 +73,33 @@ inline int vn(char op, int a, int b, long* slot) {
   if (slot) ++*slot;
   const int id = next_id++;
   memo[key] = id;
+  nodes[id] = key;
   return id;
+}
+
+// Operations on which the given results depend (what remains after a
+// compiler removes the code whose results are never used).
+inline Tally live(const std::vector<int>& outs) {
+  Tally t;
+  std::set<int> seen;
+  std::vector<int> stack(outs.begin(), outs.end());
+  while (!stack.empty()) {
+    const int id = stack.back();
+    stack.pop_back();
+    if (!seen.insert(id).second) continue;
+    auto it = nodes.find(id);
+    if (it == nodes.end()) continue;  // constant or input
+    const char op = std::get<0>(it->second);
+    if (op == '+' || op == '-') ++t.add;
+    else if (op == '*') ++t.mul;
+    else if (op == '/') ++t.div;
+    else if (op == 's') ++t.sqrt;
+    else if (op == 'e') ++t.exp;
+    else if (op == 'c') ++t.erfc;
+    stack.push_back(std::get<1>(it->second));
+    if (op != 'n' && op != 's' && op != 'e' && op != 'c') stack.push_back(std::get<2>(it->second));
+  }
+  return t;
 }
 inline Cnt operator+(Cnt a, Cnt b) {
   if (is_const(a.id, 0.0)) return b;
@@ -146,9 +176,16 @@ static void emit(int order, int nq, double pr) {
   opc::reset();
   iface_flux(qL, dqL, qR, dqR, gp, F, Ft);
   const opc::Tally face = opc::g;
+  std::vector<int> outs;
+  for (int k = 0; k < 5; ++k) outs.push_back(Ft[k].id);
+  const opc::Tally face_ft = opc::live(outs);  // the S2O4 stage-2 pass needs F_t only
   opc::reset();
   interior_flux(qL, dqL, gp, Fc, Ftc);
   const opc::Tally cell = opc::g;
+  outs.clear();
+  for (int d = 0; d < 3; ++d)
+    for (int k = 0; k < 5; ++k) outs.push_back(Ftc[d][k].id);
+  const opc::Tally cell_ft = opc::live(outs);
 
   const int NM = n_modes_(order), NT = n_tmodes_(order), NMx = n_modes_dx(order);
   // traces, per side (face) or per point (cell): per mode the basis products
@@ -165,15 +202,18 @@ static void emit(int order, int nq, double pr) {
   const long proj_cell = 3 * NMx * 5 * 2 * 2 + 30;
   const long face_total = face.flops() + 2 * trace_face_side + proj_face;
   const long cell_total = cell.flops() + trace_cell + proj_cell;
+  // F_t-only variants (stage 2 of S2O4): half of each projection
+  const long face_total_ft = face_ft.flops() + 2 * trace_face_side + 5 * NT * 2 + 5;
+  const long cell_total_ft = cell_ft.flops() + trace_cell + 3 * NMx * 5 * 2 + 15;
   printf(
       "{\"order\": %d, \"n_q\": %d, \"pr_fix\": %s, "
       "\"face_point\": {\"flux_flops\": %ld, \"div\": %ld, \"sqrt\": %ld, \"exp\": %ld, \"erfc\": %ld, "
-      "\"trace_flops\": %ld, \"proj_flops\": %ld, \"total_flops\": %ld}, "
+      "\"trace_flops\": %ld, \"proj_flops\": %ld, \"total_flops\": %ld, \"total_flops_ft\": %ld}, "
       "\"cell_point\": {\"flux_flops\": %ld, \"div\": %ld, \"sqrt\": %ld, \"exp\": %ld, \"erfc\": %ld, "
-      "\"trace_flops\": %ld, \"proj_flops\": %ld, \"total_flops\": %ld}}\n",
+      "\"trace_flops\": %ld, \"proj_flops\": %ld, \"total_flops\": %ld, \"total_flops_ft\": %ld}}\n",
       order, nq, pr != 1.0 ? "true" : "false", face.flops(), face.div, face.sqrt, face.exp, face.erfc,
-      2 * trace_face_side, proj_face, face_total, cell.flops(), cell.div, cell.sqrt, cell.exp, cell.erfc, trace_cell,
-      proj_cell, cell_total);
+      2 * trace_face_side, proj_face, face_total, face_total_ft, cell.flops(), cell.div, cell.sqrt, cell.exp,
+      cell.erfc, trace_cell, proj_cell, cell_total, cell_total_ft);
 }
 
 int main() {
