@@ -374,6 +374,7 @@ def run_ours(args):
     n = args.n
     dt = inputs.tgv_dt(n, ORDER)
     dof_step = 5 * 10 * n ** 3 * 2
+    flux_step = 2 * (3 * n ** 3 * NQ ** 2 + n ** 3 * NQ ** 3)
     Q0 = inputs.tgv_state(n, ORDER, device="cuda")
     torch.cuda.synchronize()
     peaks = measured_peaks()
@@ -450,6 +451,10 @@ def run_ours(args):
                      "roofline": roof64},
             "error": err, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": m32["launches"],
+            # companion metric: gas-kinetic flux evaluations (face and cell Gauss points, both stages;
+            # one face point counts once, with both of its time integrals)
+            "flux_evaluations_per_s": {"fp32_mixed": ranks.job_rate(flux_step, ms32 * 1e-3),
+                                       "fp64": ranks.job_rate(flux_step, ms64 * 1e-3)},
         }
         print(json.dumps(line), flush=True)
     ranks.close()
