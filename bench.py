@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed FP64 steps (default: --steps)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adjoint-n", type=int, default=64, help="cells per direction of the adjoint leg (0: skip)")
+    ap.add_argument("--adjoint-steps", type=int, default=2, help="checkpointed steps of the adjoint leg")
     return ap.parse_args()
 
 
@@ -359,6 +361,38 @@ def roofline_entry(prof, precision, n, peaks, clocks):
     }
 
 
+def run_adjoint(torch, api, n, nsteps):
+    """Gradient of the final E_k w.r.t. the initial state and mu over nsteps checkpointed FP64 steps
+    (Taylor-Green P2): time per forward and per adjoint step, checkpoint and device memory."""
+    from paper_2202_13821_b300 import autograd, inputs
+
+    dt = inputs.tgv_dt(n, ORDER)
+    free0, _ = torch.cuda.mem_get_info()
+    s = api.Solver((n,) * 3, (-math.pi,) * 3, (math.pi,) * 3, order=ORDER, gamma=GAMMA, mu=MU, Pr=PR, n_q=NQ,
+                   precision=api.DGHGKS_FP64)
+    Q0 = inputs.tgv_state(n, ORDER, device="cuda").requires_grad_(True)
+    mu = torch.tensor(MU, dtype=torch.float64, device="cuda", requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = autograd.kinetic_energy(autograd.rollout(Q0, mu, s, dt, nsteps), s)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    free1, _ = torch.cuda.mem_get_info()  # checkpoints, state and the library's scratch are held here
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    state = Q0.numel() * 8
+    out = {"workload": f"Taylor-Green {n}^3 P2 FP64, {nsteps} checkpointed S2O4 steps, dE_k/d(Q0, mu)",
+           "forward_ms_per_step": 1e3 * (t1 - t0) / nsteps, "adjoint_ms_per_step": 1e3 * (t2 - t1) / nsteps,
+           "checkpoint_bytes_per_step": state, "checkpoint_bytes_100_steps": 100 * state,
+           "device_bytes_after_forward": free0 - free1, "dJ_dmu": float(mu.grad.item()),
+           "grad_norm": float(Q0.grad.norm().item())}
+    s.close()
+    del Q0, mu, J
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -436,6 +470,8 @@ def run_ours(args):
         s_e2e.close()
         del host
 
+    adj = run_adjoint(torch, api, args.adjoint_n, args.adjoint_steps) if args.adjoint_n > 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rates, threads, sample = oracle_sample(n, args.cpu_seconds, Q=Q0.cpu().numpy())
@@ -451,6 +487,7 @@ def run_ours(args):
                      "roofline": roof64},
             "error": err, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": m32["launches"],
+            "adjoint": adj,
             # companion metric: gas-kinetic flux evaluations (face and cell Gauss points, both stages;
             # one face point counts once, with both of its time integrals)
             "flux_evaluations_per_s": {"fp32_mixed": ranks.job_rate(flux_step, ms32 * 1e-3),

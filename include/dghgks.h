@@ -121,8 +121,9 @@ int dghgks_step(dghgks_ctx* ctx, double* Q, double dt, void* stream);
 
 /* nsteps S2O4 steps in place on the device state Q, replaying a CUDA graph
  * of one step (8 kernel launches) on `stream`.  The graph is captured on a
- * private stream at the first call and re-captured when Q or dt changes
- * (the executable graph is updated in place when possible).  Results are
+ * private stream at the first call and re-captured when Q, dt or the
+ * viscosity (dghgks_set_mu) changes (the executable graph is updated in
+ * place when possible).  Results are
  * identical to nsteps calls of dghgks_step.  Asynchronous.  Must not be
  * called while `stream` itself is being captured; profiling records nothing
  * for graph replays. */

@@ -59,8 +59,9 @@ struct dghgks_ctx {
   // captured step graph
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
-  double* g_Q = nullptr;
+  double* g_Q = nullptr;  // arguments the captured graph was built with
   double g_dt = 0.0;
+  double g_mu = -1.0;
   char err[512] = {0};
 };
 
@@ -505,7 +506,9 @@ int dghgks_steps(dghgks_ctx* c, double* Q, double dt, int nsteps, void* stream) 
   if (!c->cap_stream)
     if (int rc = cuda_check(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream"))
       return rc;
-  if (!c->gexec || c->g_Q != Q || c->g_dt != dt) {
+  // the kernels' arguments (state pointer, dt and the gas parameters derived
+  // from dt and mu) are baked into the graph: capture again when one changed
+  if (!c->gexec || c->g_Q != Q || c->g_dt != dt || c->g_mu != c->mu) {
     const bool prof = c->prof;
     const int64_t launches = c->launches;
     c->prof = false;
@@ -532,6 +535,7 @@ int dghgks_steps(dghgks_ctx* c, double* Q, double dt, int nsteps, void* stream) 
     if (int rc = cuda_check(c, e, "graph instantiate")) return rc;
     c->g_Q = Q;
     c->g_dt = dt;
+    c->g_mu = c->mu;
   }
   for (int n = 0; n < nsteps; ++n)
     if (int rc = cuda_check(c, cudaGraphLaunch(c->gexec, s), "graph launch")) return rc;

@@ -138,3 +138,40 @@ def test_kinetic_energy_gradient_vs_dual_numbers_and_fd(torch, api, orc):
 
     fd = (Ek_at(h) - Ek_at(-h)) / (2 * h)
     assert abs(directional - fd) <= 1e-6 * abs(fd), (directional, fd)
+
+
+def test_adjoint_configuration_tgv32_p2_50_steps(torch, api):
+    """The adjoint configuration: Taylor-Green 32^3, P2, FP64, 50 S2O4 steps, gradient of the final
+    E_k with respect to every initial modal coefficient and mu (per-step checkpoints, stage
+    recomputation), checked against a central finite difference of the forward run along a
+    seeded Gaussian direction."""
+    from paper_2202_13821_b300 import autograd, inputs
+
+    n, N = 32, 50
+    lo, hi = (-math.pi,) * 3, (math.pi,) * 3
+    mu0 = 1 / 1600
+    dt = inputs.tgv_dt(n, 2)
+    s = api.Solver((n,) * 3, lo, hi, order=2, mu=mu0, Pr=0.72, n_q=3)
+    Q0 = inputs.tgv_state(n, 2, perturb=1e-4, device="cuda")
+    Qt = Q0.clone().requires_grad_(True)
+    mu = torch.tensor(mu0, dtype=torch.float64, device="cuda", requires_grad=True)
+    J = autograd.kinetic_energy(autograd.rollout(Qt, mu, s, dt, N), s)
+    J.backward()
+    gQ, gmu = Qt.grad, float(mu.grad.item())
+    assert torch.isfinite(gQ).all()
+    g = torch.Generator(device="cpu").manual_seed(11)
+    scale = Q0.reshape(5, -1).abs().amax(dim=1).reshape(5, 1, 1, 1, 1)
+    dQ = (torch.randn(Q0.shape, generator=g, dtype=torch.float64) * 1e-3).cuda() * scale
+    dmu = 1e-4 * mu0
+    directional = float((gQ * dQ).sum()) + gmu * dmu
+    h = 1e-3
+
+    def Ek_at(eps):
+        s.set_mu(mu0 + eps * dmu)
+        Q = Q0 + eps * dQ
+        s.steps(Q, dt, N)
+        return s.kinetic_energy(Q)
+
+    fd = (Ek_at(h) - Ek_at(-h)) / (2 * h)
+    print(f"directional derivative: adjoint {directional:.12e}, finite difference {fd:.12e}, dJ/dmu {gmu:.6e}")
+    assert abs(directional - fd) <= 1e-6 * abs(fd), (directional, fd)

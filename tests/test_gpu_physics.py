@@ -153,6 +153,22 @@ def test_deterministic_and_graph_replay_bitwise(torch, api):
         assert torch.equal(D, E)
 
 
+def test_graph_replay_follows_set_mu(torch, api):
+    """dghgks_steps after dghgks_set_mu uses the new viscosity (the graph is captured again)."""
+    from paper_2202_13821_b300 import inputs
+
+    s = api.Solver((12, 10, 8), **TGV, order=2, mu=1 / 1600, Pr=0.72)
+    Q0 = inputs.tgv_state((12, 10, 8), 2, perturb=1e-3, device="cuda")
+    A, B = Q0.clone(), Q0.clone()
+    s.steps(A, 4e-3, 2)  # capture with the first viscosity
+    s.set_mu(1 / 400)
+    A = Q0.clone()
+    s.steps(A, 4e-3, 2)
+    s.step(B, 4e-3, 2)
+    s.status()
+    assert torch.equal(A, B)
+
+
 def test_fp32_mixed_error_against_fp64(torch, api):
     """Stated error of the FP32-mixed path on the Taylor-Green vortex (48^3, 10 steps)."""
     from paper_2202_13821_b300 import inputs
