@@ -10,70 +10,18 @@
 //   cotangent of F and F_t at every Gauss point; the point-flux Jacobian
 //   transposed gives the cotangents of the traces and of the viscosity; the
 //   trace transposed gives the cotangent of Q.
-// The point-flux Jacobian-transpose products use forward-mode dual numbers
-// through the same templated flux code as the forward kernels: one dual pass
-// per input direction (41 at a face point: both sides' traces and
-// gradients and mu; 21 at a cell point), each dotted with the point's flux
-// cotangent.  Exact to rounding; every sum is taken in a fixed order.
+// The point-flux Jacobian-transpose products are the hand-written reverse
+// mode of gks_point_adj.cuh: one backward sweep per Gauss point, after
+// recomputing the point's forward intermediates.  Exact to rounding; every
+// sum is taken in a fixed order.
 #pragma once
 #include <cmath>
 
 #include "adjoint.h"
 #include "dg_kernels.cuh"
+#include "gks_point_adj.cuh"
 
 namespace dghgks {
-
-// ---- forward-mode dual number (value, one directional derivative) ----
-struct DualD {
-  double v, d;
-  DG_HD DualD() : v(0.0), d(0.0) {}
-  DG_HD DualD(double x) : v(x), d(0.0) {}
-  DG_HD DualD(double x, double dx) : v(x), d(dx) {}
-};
-DG_HD DualD operator+(DualD a, DualD b) { return DualD(a.v + b.v, a.d + b.d); }
-DG_HD DualD operator-(DualD a, DualD b) { return DualD(a.v - b.v, a.d - b.d); }
-DG_HD DualD operator-(DualD a) { return DualD(-a.v, -a.d); }
-DG_HD DualD operator*(DualD a, DualD b) { return DualD(a.v * b.v, a.d * b.v + a.v * b.d); }
-DG_HD DualD operator/(DualD a, DualD b) {
-  const double q = a.v / b.v;
-  return DualD(q, (a.d - q * b.d) / b.v);
-}
-DG_HD DualD& operator+=(DualD& a, DualD b) {
-  a = a + b;
-  return a;
-}
-DG_HD bool operator>(DualD a, DualD b) { return a.v > b.v; }
-DG_HD bool operator<(DualD a, DualD b) { return a.v < b.v; }
-DG_HD bool operator!=(DualD a, DualD b) { return a.v != b.v; }
-DG_HD DualD exp(DualD a) {
-  const double e = ::exp(a.v);
-  return DualD(e, e * a.d);
-}
-DG_HD DualD sqrt(DualD a) {
-  const double r = ::sqrt(a.v);
-  return DualD(r, a.d / (2.0 * r));
-}
-DG_HD DualD erfc(DualD a) {
-  // d/dx erfc(x) = -2/sqrt(pi) exp(-x^2)
-  return DualD(::erfc(a.v), -1.12837916709551257390 * ::exp(-a.v * a.v) * a.d);
-}
-
-// sums += constant side sums (zero tangents)
-DG_HD void add_sums(SideSums<DualD>& a, const SideSums<double>& b) {
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    a.Q0[k] += DualD(b.Q0[k]);
-    a.V4[k] += DualD(b.V4[k]);
-    a.V5[k] += DualD(b.V5[k]);
-    a.V6[k] += DualD(b.V6[k]);
-    a.W5[k] += DualD(b.W5[k]);
-    a.W6[k] += DualD(b.W6[k]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) a.dQ0[i][k] += DualD(b.dQ0[i][k]);
-  }
-}
-
-
 
 template <int ORDER, int NQ>
 struct FaceAdjSmem {
@@ -188,12 +136,9 @@ __global__ void __launch_bounds__(FB* NQ* NQ)
     }
   }
 
-  // 41 directions: traces of both sides (q: 5, dq: 15 each) and mu.  A
-  // direction seeds one side only, so the other side's sums are taken from a
-  // plain FP64 pass and only the seeded side (and the finish) runs in dual
-  // numbers.
-  const bool pr_fix = (gp.pr_fix != 0.0);
-  SideSums<double> s0[2];
+  // Reverse mode of the point flux (gks_point_adj.cuh): the cotangents of
+  // F, F_t in the local frame give those of both sides' traces and of mu in
+  // one backward sweep.
   double ql0[2][5], dql0[2][3][5];
   {
     const int ax[3] = {A0, A1, A2};
@@ -212,61 +157,24 @@ __global__ void __launch_bounds__(FB* NQ* NQ)
         dql0[side][ii][3] = dq[side][ax[ii]][1 + A2];
         dql0[side][ii][4] = dq[side][ax[ii]][4];
       }
-      iface_zero(s0[side]);
     }
-    iface_side<double, +1>(ql0[0], dql0[0], gp, pr_fix, s0[0]);
-    iface_side<double, -1>(ql0[1], dql0[1], gp, pr_fix, s0[1]);
   }
-  // local index of a global momentum component
+  const double Flb[5] = {lF[0], lF[1 + A0], lF[1 + A1], lF[1 + A2], lF[4]};
+  const double Ftlb[5] = {lT[0], lT[1 + A0], lT[1 + A1], lT[1 + A2], lT[4]};
+  double qlb[2][5], dqlb[2][3][5], gmu = 0.0;
+  iface_flux_vjp(ql0[0], dql0[0], ql0[1], dql0[1], gp, Flb, Ftlb, qlb[0], dqlb[0], qlb[1], dqlb[1], gmu);
+  if (!active) gmu = 0.0;
+  // back to global variables and axes: local index of a global momentum component
   const int loc[3] = {(0 - A0 + 3) % 3, (1 - A0 + 3) % 3, (2 - A0 + 3) % 3};
-  double gmu = 0.0;
-  GasPar<DualD> gd;
-  gd.K = DualD(gp.K);
-  gd.gm1 = DualD(gp.gm1);
-  gd.tau_add = DualD(gp.tau_add);
-  gd.pr_fix = DualD(gp.pr_fix);
-  gd.dt = DualD(gp.dt);
-  gd.inv_dt = DualD(gp.inv_dt);
-  for (int dir = 0; dir < 41; ++dir) {
-    gd.mu = DualD(gp.mu, dir == 40 ? 1.0 : 0.0);
-    const int side = dir < 20 ? 0 : 1;
-    const int r = dir - 20 * side;  // 0..4: q[v]; 5..19: dq[d][v] (global d, v)
-    SideSums<DualD> sums;
-    if (dir < 40) {
-      // seed the input in the local frame: global variable v -> local component
-      const int v = r < 5 ? r : (r - 5) % 5;
+#pragma unroll
+  for (int side = 0; side < 2; ++side)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
       const int lv = (v >= 1 && v <= 3) ? 1 + loc[v - 1] : v;
-      const int li = r < 5 ? -1 : loc[(r - 5) / 5];  // local derivative index
-      DualD ql[5], dql[3][5];
+      gs[side * 20 + v][p][f] = active ? qlb[side][lv] : 0.0;
 #pragma unroll
-      for (int k2 = 0; k2 < 5; ++k2) {
-        ql[k2] = DualD(ql0[side][k2], (li < 0 && k2 == lv) ? 1.0 : 0.0);
-#pragma unroll
-        for (int ii = 0; ii < 3; ++ii) dql[ii][k2] = DualD(dql0[side][ii][k2], (ii == li && k2 == lv) ? 1.0 : 0.0);
-      }
-      iface_zero(sums);
-      if (side == 0)
-        iface_side<DualD, +1>(ql, dql, gd, pr_fix, sums);
-      else
-        iface_side<DualD, -1>(ql, dql, gd, pr_fix, sums);
-      add_sums(sums, s0[1 - side]);
-    } else {
-      iface_zero(sums);
-      add_sums(sums, s0[0]);
-      add_sums(sums, s0[1]);
+      for (int d = 0; d < 3; ++d) gs[side * 20 + 5 + d * 5 + v][p][f] = active ? dqlb[side][loc[d]][lv] : 0.0;
     }
-    DualD Fl[5], Ftl[5];
-    iface_finish(sums, gd, Fl, Ftl);
-    // back to global components and dot with the cotangents
-    double gi = lF[0] * Fl[0].d + lF[4] * Fl[4].d + lT[0] * Ftl[0].d + lT[4] * Ftl[4].d;
-    gi += lF[1 + A0] * Fl[1].d + lF[1 + A1] * Fl[2].d + lF[1 + A2] * Fl[3].d;
-    gi += lT[1 + A0] * Ftl[1].d + lT[1 + A1] * Ftl[2].d + lT[1 + A2] * Ftl[3].d;
-    if (!active) gi = 0.0;
-    if (dir < 40)
-      gs[dir][p][f] = gi;
-    else
-      gmu = gi;
-  }
   red[p][f] = gmu;
   __syncthreads();
 
@@ -312,8 +220,7 @@ struct CellAdjSmem {
   static constexpr int NOP2 = (NC + LY::PG - 1) / LY::PG * LY::PG;
   static constexpr size_t coef = sizeof(double) * NC * CB;
   static constexpr size_t red = sizeof(double) * CB * NOP2;
-  static constexpr size_t gsc = sizeof(double) * 20 * LY::WARPS * 32;
-  static constexpr size_t bytes = 3 * coef + red + sizeof(double) * LY::WARPS * 32 + gsc;
+  static constexpr size_t bytes = 3 * coef + red + sizeof(double) * LY::WARPS * 32;
 };
 
 template <int ORDER, int NQ>
@@ -330,8 +237,6 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
   double(*cmuT)[CB] = reinterpret_cast<double(*)[CB]>(smem_raw + 2 * S::coef);
   double(*red)[NOP2] = reinterpret_cast<double(*)[NOP2]>(smem_raw + 3 * S::coef);
   double* mured = reinterpret_cast<double*>(smem_raw + 3 * S::coef + S::red);
-  double(*gsc)[LY::WARPS * 32] =
-      reinterpret_cast<double(*)[LY::WARPS * 32]>(smem_raw + 3 * S::coef + S::red + sizeof(double) * LY::WARPS * 32);
 
   const int tid = threadIdx.x, nthr = LY::WARPS * 32;
   const int lane = tid & 31, lg = lane % PG;
@@ -402,45 +307,17 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
     }
   }
 
-  // 21 directions: q (5), dq (15), mu; the input cotangents go through
-  // shared memory (indexed by direction) to keep the loop body small
-  double gmu = 0.0;
-  GasPar<DualD> gd;
-  gd.K = DualD(gp.K);
-  gd.gm1 = DualD(gp.gm1);
-  gd.tau_add = DualD(gp.tau_add);
-  gd.pr_fix = DualD(gp.pr_fix);
-  gd.dt = DualD(gp.dt);
-  gd.inv_dt = DualD(gp.inv_dt);
-  #pragma unroll 1
-  for (int dir = 0; dir < 21; ++dir) {
-    double gi = 0.0;
-    if (active) {
-      gd.mu = DualD(gp.mu, dir == 20 ? 1.0 : 0.0);
-      DualD qd[5], dqd[3][5], F[3][5], Ft[3][5];
+  // reverse mode of the interior flux (gks_point_adj.cuh): one backward sweep
+  double gq[5], gdq[3][5], gmu = 0.0;
+  interior_flux_vjp(q, dq, gp, lF, lT, gq, gdq, gmu);
+  if (!active) {
+    gmu = 0.0;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        qd[v] = DualD(q[v], dir == v ? 1.0 : 0.0);
+    for (int v = 0; v < 5; ++v) {
+      gq[v] = 0.0;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) dqd[d][v] = DualD(dq[d][v], dir == 5 + d * 5 + v ? 1.0 : 0.0);
-      }
-      interior_flux(qd, dqd, gd, F, Ft);
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int v = 0; v < 5; ++v) gi += lF[d][v] * F[d][v].d + lT[d][v] * Ft[d][v].d;
+      for (int d = 0; d < 3; ++d) gdq[d][v] = 0.0;
     }
-    if (dir < 20)
-      gsc[dir][tid] = gi;
-    else
-      gmu = gi;
-  }
-  double gq[5], gdq[3][5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    gq[v] = gsc[v][tid];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) gdq[d][v] = gsc[5 + d * 5 + v][tid];
   }
   mured[tid] = gmu;
 
