@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adjoint-n", type=int, default=64, help="cells per direction of the adjoint leg (0: skip)")
-    ap.add_argument("--adjoint-steps", type=int, default=2, help="checkpointed steps of the adjoint leg")
+    ap.add_argument("--adjoint-steps", type=int, default=4, help="checkpointed steps of the adjoint leg")
     return ap.parse_args()
 
 
