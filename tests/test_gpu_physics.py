@@ -197,6 +197,35 @@ def test_fp32_mixed_error_against_fp64(torch, api):
     assert l2 < 0.5 * change
 
 
+def test_fp32_mixed_error_128_cubed(torch, api):
+    """The FP32-mixed configuration: Taylor-Green 128^3 P2, 20 steps in FP32-mixed and in FP64 on the
+    same GPU (the FP64 path equals the oracle to 1e-11): stated L2 density difference and relative
+    E_k-history difference."""
+    from paper_2202_13821_b300 import inputs
+
+    n, N = 128, 20
+    dt = inputs.tgv_dt(n, 2)
+    Q0 = inputs.tgv_state(n, 2, device="cuda")
+    res = {}
+    for prec in (0, 1):
+        s = api.Solver((n,) * 3, **TGV, order=2, mu=1 / 1600, Pr=0.72, precision=prec)
+        Q = Q0.clone()
+        ek = [s.kinetic_energy(Q)]
+        for _ in range(N):
+            s.steps(Q, dt, 1)
+            ek.append(s.kinetic_energy(Q))
+        s.status()
+        res[prec] = (Q, np.array(ek), s)
+    s64 = res[0][2]
+    l2 = s64.l2_diff(res[1][0], res[0][0], 0)
+    change = s64.l2_diff(res[0][0], Q0, 0)
+    dek = np.abs(res[1][1] - res[0][1]) / res[0][1]
+    print(f"128^3, {N} steps: L2(rho) FP32-mixed vs FP64 {l2:.3e} (FP64 change {change:.3e}), "
+          f"max relative E_k difference {dek.max():.3e}")
+    assert dek.max() < 1e-8
+    assert l2 < 0.5 * change
+
+
 def test_nonphysical_state_sets_flag_and_context_survives(torch, api):
     from paper_2202_13821_b300 import inputs
 
