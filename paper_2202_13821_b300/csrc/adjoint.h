@@ -29,7 +29,8 @@ void adjoint_vjp(int order, int nq, const double* Q, const GasPar<double>& g, co
 // *acc += sum of the n partials (fixed order)
 void adjoint_mu_sum(const double* part, long long n, double* acc, cudaStream_t s);
 // gradient of E_k with respect to Q (scale = |K| / (rho0 |Omega|))
-void adjoint_ek_vjp(int order, int nq, const double* Q, long long nc, double scale, double* out, cudaStream_t s);
+// dE_k/dQ; scale = 1/(rho0 |Omega|) times |K| on a uniform mesh (a rectilinear mesh weights each cell by its volume)
+void adjoint_ek_vjp(int order, int nq, const double* Q, const MeshDev& m, double scale, double* out, cudaStream_t s);
 // number of launches one adjoint_vjp makes
 constexpr int kAdjointLaunches = 4;
 

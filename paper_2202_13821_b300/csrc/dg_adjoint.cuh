@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ)
         if (D == 2) ck = wrapm(k - 1, nz);
       }
       const size_t idx = (size_t)c * nc + ((size_t)ck * ny + cj) * nx + ci;
-      const double iM = inv_mass(c % NM, m.vol);
+      const double iM = inv_mass(c % NM, cell_vol64(m, ci, cj, ck));
       const double a = io.lamA[idx], b = io.lamB ? io.lamB[idx] : 0.0;
       q = Q[idx];
       mR = iM * (io.cLA * a + io.cLB * b);
@@ -98,8 +98,13 @@ __global__ void __launch_bounds__(FB* NQ* NQ)
     Lb[n] = leg<double>(n, xb);
     dLb[n] = dleg<double>(n, xb);
   }
-  const double sD = 2.0 / m.h[D], s1 = 2.0 / m.h[T1], s2 = 2.0 / m.h[T2];
-  const double w = active ? gauss_w(NQ, a) * gauss_w(NQ, b) * (m.vol / m.h[D]) : 0.0;
+  // gradient scales: along D those of the left and right cells, tangential
+  // ones shared by both cells (rectilinear mesh); the face area
+  const int cidx[3] = {active ? i : 0, j, k};
+  const int nAx = D == 0 ? nx : (D == 1 ? ny : nz);
+  const double sDs[2] = {cell_sc<double>(m, D, wrapm(cidx[D] - 1, nAx)), cell_sc<double>(m, D, cidx[D])};
+  const double s1 = cell_sc<double>(m, T1, cidx[T1]), s2 = cell_sc<double>(m, T2, cidx[T2]);
+  const double w = active ? gauss_w(NQ, a) * gauss_w(NQ, b) * face_area<double>(m, D, cidx[T1], cidx[T2]) : 0.0;
 
   // traces (global axes) and the flux cotangents of the point
   double q[2][5], dq[2][3][5], lF[5], lT[5];
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ)
         lT[v] += sg * B * cmu[side * 2 + 1][v * NM + mm][f];
       }
       q[side][v] = s0;
-      dq[side][D][v] = gD * sD;
+      dq[side][D][v] = gD * sDs[side];
       dq[side][T1][v] = g1 * s1;
       dq[side][T2][v] = g2 * s2;
     }
@@ -193,7 +198,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ)
         const double l1 = leg<double>(n1, xa2), l2 = leg<double>(n2, xb2);
         const int base = side * 20;
         acc += pn * l1 * l2 * gs[base + v][pp][f];
-        acc += sD * dpn * l1 * l2 * gs[base + 5 + D * 5 + v][pp][f];
+        acc += sDs[side] * dpn * l1 * l2 * gs[base + 5 + D * 5 + v][pp][f];
         acc += s1 * pn * dleg<double>(n1, xa2) * l2 * gs[base + 5 + T1 * 5 + v][pp][f];
         acc += s2 * pn * l1 * dleg<double>(n2, xb2) * gs[base + 5 + T2 * 5 + v][pp][f];
       }
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
     double q = 0, mR = 0, mT = 0;
     if (i < nx) {
       const size_t idx = (size_t)comp * nc + row + i;
-      const double iM = inv_mass(comp % NM, m.vol);
+      const double iM = inv_mass(comp % NM, cell_vol64(m, i, j, k));
       const double a = io.lamA[idx], b = io.lamB ? io.lamB[idx] : 0.0;
       q = Q[idx];
       mR = iM * (io.cLA * a + io.cLB * b);
@@ -276,8 +281,10 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
       dL1[d][n] = dleg<double>(n, x);
     }
   }
-  const double sc[3] = {2.0 / m.h[0], 2.0 / m.h[1], 2.0 / m.h[2]};
-  const double w = active ? gauss_w(NQ, pa[0]) * gauss_w(NQ, pa[1]) * gauss_w(NQ, pa[2]) * m.vol : 0.0;
+  const int icell = (i0 + cb < nx) ? i0 + cb : nx - 1;
+  const double sc[3] = {cell_sc<double>(m, 0, icell), cell_sc<double>(m, 1, j), cell_sc<double>(m, 2, k)};
+  const double w =
+      active ? gauss_w(NQ, pa[0]) * gauss_w(NQ, pa[1]) * gauss_w(NQ, pa[2]) * cell_vol64(m, icell, j, k) : 0.0;
 
   // traces and flux cotangents: lambda_F_d[v] = w (2/h_d) sum_n dB_n/dr_d mu_R[v][n]
   double q[5], dq[3][5], lF[3][5], lT[3][5];
@@ -381,10 +388,12 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
 // de/drho = -|m|^2/(2 rho^2), de/dm_d = m_d / rho, de/drhoE = 0.
 // ---------------------------------------------------------------------------
 template <int ORDER, int NQ>
-__global__ void __launch_bounds__(RED_THREADS) k_ek_vjp(const double* __restrict__ Q, long long nc, double scale,
+__global__ void __launch_bounds__(RED_THREADS) k_ek_vjp(const double* __restrict__ Q, const MeshDev m, double scale,
                                                         double* __restrict__ out) {
   constexpr int NM = n_modes(ORDER);
+  const long long nc = m.ncell;
   for (long long c = (long long)blockIdx.x * RED_THREADS + threadIdx.x; c < nc; c += (long long)gridDim.x * RED_THREADS) {
+    const double cw = cell_weight(m, c) * scale;  // |K| / (rho0 |Omega|) (|K| in scale on a uniform mesh)
     double co[4][NM], g[5][NM];
 #pragma unroll
     for (int v = 0; v < 4; ++v)
@@ -408,7 +417,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_ek_vjp(const double* __restrict
 #pragma unroll
             for (int v = 0; v < 4; ++v) qv[v] += co[v][mm] * B[mm];
           }
-          const double wq = gauss_w(NQ, a) * gauss_w(NQ, b) * gauss_w(NQ, cz) * scale;
+          const double wq = gauss_w(NQ, a) * gauss_w(NQ, b) * gauss_w(NQ, cz) * cw;
           const double ir = 1.0 / qv[0];
           const double m2 = qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
           const double de[4] = {-0.5 * m2 * ir * ir, qv[1] * ir, qv[2] * ir, qv[3] * ir};

@@ -124,6 +124,10 @@ template <class R>
 __device__ __forceinline__ R face_area(const MeshDev& m, int d, int c1, int c2) {
   return mesh_nonuniform(m) ? cell_w<R>(m, tan1(d), c1) * cell_w<R>(m, tan2(d), c2) : mesh_area<R>(m, d);
 }
+// FP64 volume of cell (i, j, k)
+__device__ __forceinline__ double cell_vol64(const MeshDev& m, int i, int j, int k) {
+  return mesh_nonuniform(m) ? __ldg(m.geo64[0] + i) * __ldg(m.geo64[1] + j) * __ldg(m.geo64[2] + k) : m.vol;
+}
 // FP64 volume of cell c (linear index) on a rectilinear mesh; 1 on a uniform
 // mesh, where the reductions scale by the common volume at the end
 __device__ __forceinline__ double cell_weight(const MeshDev& m, long long c) {

@@ -55,10 +55,11 @@ void adjoint_mu_sum(const double* part, long long n, double* acc, cudaStream_t s
   k_mu_sum<<<1, RED_THREADS, 0, s>>>(part, n, acc);
 }
 
-void adjoint_ek_vjp(int order, int nq, const double* Q, long long nc, double scale, double* out, cudaStream_t s) {
-  if (order == 1 && nq == 2) k_ek_vjp<1, 2><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, nc, scale, out);
-  else if (order == 2 && nq == 2) k_ek_vjp<2, 2><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, nc, scale, out);
-  else if (order == 2 && nq == 3) k_ek_vjp<2, 3><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, nc, scale, out);
+void adjoint_ek_vjp(int order, int nq, const double* Q, const MeshDev& m, double scale, double* out,
+                    cudaStream_t s) {
+  if (order == 1 && nq == 2) k_ek_vjp<1, 2><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, m, scale, out);
+  else if (order == 2 && nq == 2) k_ek_vjp<2, 2><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, m, scale, out);
+  else if (order == 2 && nq == 3) k_ek_vjp<2, 3><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, m, scale, out);
 }
 
 }  // namespace dghgks

@@ -686,7 +686,6 @@ int dghgks_profile_read(dghgks_ctx* c, double* ms, int64_t* launches) {
 
 static int adj_prepare(dghgks_ctx* c) {
   if (c->precision != DGHGKS_FP64) return fail(c, DGHGKS_EUNSUP, "the adjoint needs an FP64 context");
-  if (c->nonuniform) return fail(c, DGHGKS_EUNSUP, "the adjoint supports uniform meshes only");
   if (c->order > 2) return fail(c, DGHGKS_EUNSUP, "the adjoint supports orders 1 and 2");
   if (c->adjH) return DGHGKS_OK;
   const size_t nc = (size_t)c->ncell;
@@ -771,10 +770,10 @@ int dghgks_adjoint_step(dghgks_ctx* c, const double* Qn, const double* lam_next,
 int dghgks_kinetic_energy_vjp(dghgks_ctx* c, const double* Q, double rho0, double* dEk_dQ, void* stream) {
   if (!c) return DGHGKS_EARG;
   if (c->order > 2) return fail(c, DGHGKS_EUNSUP, "the adjoint supports orders 1 and 2");
-  if (c->nonuniform) return fail(c, DGHGKS_EUNSUP, "the adjoint supports uniform meshes only");
   if (!Q || !dEk_dQ || dEk_dQ == Q) return fail(c, DGHGKS_EARG, "bad argument");
   if (!(rho0 > 0)) return fail(c, DGHGKS_EARG, "rho0 must be > 0");
-  adjoint_ek_vjp(c->order, c->nq, Q, c->ncell, c->vol / (rho0 * c->omega), dEk_dQ, static_cast<cudaStream_t>(stream));
+  adjoint_ek_vjp(c->order, c->nq, Q, mesh_dev(c), vol_scale(c) / (rho0 * c->omega), dEk_dQ,
+                 static_cast<cudaStream_t>(stream));
   c->launches += 1;
   return after_launch(c, "E_k VJP launch");
 }

@@ -44,6 +44,8 @@ def direction(shape, seed, Q):
 
 CASES = [
     dict(order=1, nq=2, n=(5, 4, 3), mu=5e-3, Pr=1.0, tau_eps=0.0, state="random"),
+    dict(order=2, nq=3, n=(4, 5, 3), mu=1e-2, Pr=0.72, tau_eps=0.0, state="random", nodes=True),
+    dict(order=1, nq=2, n=(6, 5, 4), mu=2e-3, Pr=1.0, tau_eps=0.01, state="adv", nodes=True),
     dict(order=2, nq=3, n=(4, 3, 5), mu=1e-2, Pr=0.72, tau_eps=0.0, state="random"),
     dict(order=2, nq=2, n=(6, 5, 4), mu=1 / 1600, Pr=0.72, tau_eps=0.0, state="tgv"),
     dict(order=1, nq=2, n=(6, 6, 6), mu=0.0, Pr=1.0, tau_eps=0.01, state="adv"),
@@ -62,13 +64,20 @@ def make_case(api, orc, c):
     else:
         lo, hi = (0.0,) * 3, (1.0, 0.8, 0.6)
         Q = inputs.random_state(c["n"], c["order"], seed=21)
-    s = api.Solver(c["n"], lo, hi, order=c["order"], mu=c["mu"], Pr=c["Pr"], n_q=c["nq"], tau_eps=c["tau_eps"])
+    nodes = None
+    if c.get("nodes"):  # rectilinear mesh: random widths (+-40 %) on every axis
+        nodes = tuple(inputs.random_nodes(c["n"][d], lo[d], hi[d], spread=0.4, seed=70 + d) for d in range(3))
+        if c["state"] == "adv":
+            Q = inputs.advection_state(c["n"], c["order"], perturb=1e-3, nodes=nodes)
+    s = api.Solver(c["n"], lo, hi, order=c["order"], mu=c["mu"], Pr=c["Pr"], n_q=c["nq"], tau_eps=c["tau_eps"],
+                   nodes=nodes)
     pb = orc.Problem(order=c["order"], nq=c["nq"], n=tuple(c["n"]), lo=lo, hi=hi, mu=c["mu"], Pr=c["Pr"],
-                     tau_eps=c["tau_eps"])
+                     tau_eps=c["tau_eps"], nodes=nodes)
     return s, pb, Q
 
 
-@pytest.mark.parametrize("case", CASES, ids=lambda c: f"P{c['order']}nq{c['nq']}-{c['state']}-Pr{c['Pr']}")
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"P{c['order']}nq{c['nq']}-{c['state']}-Pr{c['Pr']}"
+                                                    + ("-rect" if c.get("nodes") else ""))
 def test_residual_vjp_dot_product(torch, api, orc, case):
     s, pb, Q = make_case(api, orc, case)
     dt = 3e-3
@@ -88,7 +97,8 @@ def test_residual_vjp_dot_product(torch, api, orc, case):
     assert abs(lhs - rhs) <= 1e-10 * scale, (lhs, rhs, scale)
 
 
-@pytest.mark.parametrize("case", CASES[1:3], ids=lambda c: f"P{c['order']}-{c['state']}")
+@pytest.mark.parametrize("case", CASES[1:5], ids=lambda c: f"P{c['order']}-{c['state']}"
+                                                        + ("-rect" if c.get("nodes") else ""))
 def test_adjoint_step_dot_product(torch, api, orc, case):
     s, pb, Q = make_case(api, orc, case)
     dt = 2e-3
@@ -106,15 +116,18 @@ def test_adjoint_step_dot_product(torch, api, orc, case):
     assert abs(lhs - rhs) <= 1e-10 * scale, (lhs, rhs)
 
 
-def test_kinetic_energy_gradient_vs_dual_numbers_and_fd(torch, api, orc):
-    """E_k after 4 steps, 8^3 P1, gradient w.r.t. Q^0 and mu (FD along a seeded Gaussian direction)."""
+@pytest.mark.parametrize("rect", [False, True], ids=["uniform", "rect"])
+def test_kinetic_energy_gradient_vs_dual_numbers_and_fd(torch, api, orc, rect):
+    """E_k after 4 steps, 8^3 P1, gradient w.r.t. Q^0 and mu (FD along a seeded Gaussian direction);
+    uniform mesh, and the mapped grid of Sec. 5.1 on the three axes."""
     from paper_2202_13821_b300 import autograd, inputs
 
     n, lo, hi = (8, 8, 8), (-math.pi,) * 3, (math.pi,) * 3
+    nodes = tuple(-math.pi + math.pi * inputs.mapped_nodes(8) for _ in range(3)) if rect else None
     mu0, dt, N = 2e-2, 4e-3, 4
-    Q0 = inputs.modal_state(inputs.tgv_prim, n, 1, lo, hi, perturb=1e-3, prim_kw=dict(Ma=0.3))
-    s = api.Solver(n, lo, hi, order=1, mu=mu0, Pr=0.72, n_q=2)
-    pb = orc.Problem(order=1, nq=2, n=n, lo=lo, hi=hi, mu=mu0, Pr=0.72)
+    Q0 = inputs.modal_state(inputs.tgv_prim, n, 1, lo, hi, perturb=1e-3, prim_kw=dict(Ma=0.3), nodes=nodes)
+    s = api.Solver(n, lo, hi, order=1, mu=mu0, Pr=0.72, n_q=2, nodes=nodes)
+    pb = orc.Problem(order=1, nq=2, n=n, lo=lo, hi=hi, mu=mu0, Pr=0.72, nodes=nodes)
     Qt = torch.from_numpy(Q0).cuda().requires_grad_(True)
     mu = torch.tensor(mu0, dtype=torch.float64, device="cuda", requires_grad=True)
     J = autograd.kinetic_energy(autograd.rollout(Qt, mu, s, dt, N), s)
