@@ -163,11 +163,12 @@ int dghgks_status(dghgks_ctx* ctx, void* stream);
 
 /* ---- adjoint (reverse mode, FP64 contexts only; the paper has none) ----
  * The vector-Jacobian products below are exact to rounding: the point-flux
- * Jacobians come from forward-mode dual numbers through the same flux code,
- * the projection and trace operators are transposed exactly.  They allocate
+ * Jacobian transposes are a hand-written reverse mode of the flux code (one
+ * backward sweep per Gauss point), the projection and trace operators are
+ * transposed exactly.  Uniform and rectilinear meshes.  They allocate
  * adjoint scratch on first use (face cotangents 3 x 2 x 5 N_m doubles per
  * cell, a state-sized buffer, per-CTA partials).  FP32-mixed contexts and
- * order 3 return DGHGKS_EUNSUP. */
+ * order 3 with n_q = 4 return DGHGKS_EUNSUP. */
 
 /* (lamQ, dmu) = (dL/dQ, dL/dmu)^T lamL + (dL_t/dQ, dL_t/dmu)^T lamLt at Q for
  * the residual of dghgks_residual with the same dt.  lamQ (device, state

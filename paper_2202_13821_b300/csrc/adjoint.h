@@ -24,6 +24,8 @@ struct AdjIO {
 // shared-memory attributes of the adjoint kernels of (order, n_q)
 cudaError_t adjoint_set_attrs(int order, int nq);
 // one residual VJP (3 face launches + 1 cell launch); mu partials at io.mu_part
+// CTAs of one face-VJP launch (their viscosity partials are indexed by CTA)
+long long adjoint_face_ctas(int order, int nx, int ny, int nz);
 void adjoint_vjp(int order, int nq, const double* Q, const GasPar<double>& g, const MeshDev& m, const AdjIO& io,
                  cudaStream_t s);
 // *acc += sum of the n partials (fixed order)

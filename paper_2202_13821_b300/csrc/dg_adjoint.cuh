@@ -23,12 +23,20 @@
 
 namespace dghgks {
 
+// faces per CTA of the face VJP: 32, or 16 for P3 (its shared-memory staging
+// of both cells' coefficients and cotangents would not fit 227 KB at 32)
+template <int ORDER>
+constexpr int adj_fb() {
+  return ORDER >= 3 ? 16 : FB;
+}
+
 template <int ORDER, int NQ>
 struct FaceAdjSmem {
+  static constexpr int FBA = adj_fb<ORDER>();
   static constexpr int NM = n_modes(ORDER), NP = NQ * NQ, NC = 5 * NM;
-  static constexpr size_t coef = sizeof(double) * NC * FB;  // one side, one array
-  static constexpr size_t g = sizeof(double) * 40 * NP * FB;
-  static constexpr size_t red = sizeof(double) * FB * NP;
+  static constexpr size_t coef = sizeof(double) * NC * FBA;  // one side, one array
+  static constexpr size_t g = sizeof(double) * 40 * NP * FBA;
+  static constexpr size_t red = sizeof(double) * FBA * NP;
   static constexpr size_t bytes = 2 * coef + 4 * coef + g + red + sizeof(double) * NM;
 };
 
@@ -42,28 +50,29 @@ DG_HD double inv_mass(int mm, double vol) {
 // trace transpose of the traces' cotangents; mu_part[block] = viscosity part.
 // ---------------------------------------------------------------------------
 template <int ORDER, int NQ, int D>
-__global__ void __launch_bounds__(FB* NQ* NQ)
+__global__ void __launch_bounds__(adj_fb<ORDER>() * NQ * NQ)
     k_face_vjp(const double* __restrict__ Q, const GasPar<double> gp, const MeshDev m, const AdjIO io,
                const size_t mu_offset) {
   using S = FaceAdjSmem<ORDER, NQ>;
+  constexpr int FBA = S::FBA;
   constexpr int NM = S::NM, NP = S::NP, NC = S::NC;
   constexpr int T1 = tan1(D), T2 = tan2(D);
   constexpr int A0 = D, A1 = (D + 1) % 3, A2 = (D + 2) % 3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double(*cq)[NC][FB] = reinterpret_cast<double(*)[NC][FB]>(smem_raw);                  // [side]
-  double(*cmu)[NC][FB] = reinterpret_cast<double(*)[NC][FB]>(smem_raw + 2 * S::coef);   // [side*2 + kind]
-  double(*gs)[NP][FB] = reinterpret_cast<double(*)[NP][FB]>(smem_raw + 6 * S::coef);   // [input][point]
-  double(*red)[FB] = reinterpret_cast<double(*)[FB]>(smem_raw + 6 * S::coef + S::g);  // [point]
+  double(*cq)[NC][FBA] = reinterpret_cast<double(*)[NC][FBA]>(smem_raw);                  // [side]
+  double(*cmu)[NC][FBA] = reinterpret_cast<double(*)[NC][FBA]>(smem_raw + 2 * S::coef);   // [side*2 + kind]
+  double(*gs)[NP][FBA] = reinterpret_cast<double(*)[NP][FBA]>(smem_raw + 6 * S::coef);   // [input][point]
+  double(*red)[FBA] = reinterpret_cast<double(*)[FBA]>(smem_raw + 6 * S::coef + S::g);  // [point]
 
-  const int tid = threadIdx.x, nthr = FB * NP;
-  const int f = tid % FB, p = tid / FB;
-  const int i0 = blockIdx.x * FB, j = blockIdx.y, k = blockIdx.z;
+  const int tid = threadIdx.x, nthr = FBA * NP;
+  const int f = tid % FBA, p = tid / FBA;
+  const int i0 = blockIdx.x * FBA, j = blockIdx.y, k = blockIdx.z;
   const int nx = m.nx, ny = m.ny, nz = m.nz;
   const long long nc = m.ncell;
 
   // stage Q and the mass-scaled cotangents of both cells of each face
-  for (int e = tid; e < 2 * NC * FB; e += nthr) {
-    const int ff = e % FB, rest = e / FB, c = rest % NC, side = rest / NC;
+  for (int e = tid; e < 2 * NC * FBA; e += nthr) {
+    const int ff = e % FBA, rest = e / FBA, c = rest % NC, side = rest / NC;
     const int i = i0 + ff;
     double q = 0, mR = 0, mT = 0;
     if (i < nx) {
@@ -209,7 +218,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ)
   if (tid == 0) {
     double s = 0.0;
     for (int pp = 0; pp < NP; ++pp)
-      for (int ff = 0; ff < FB; ++ff) s += red[pp][ff];
+      for (int ff = 0; ff < FBA; ++ff) s += red[pp][ff];
     const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     io.mu_part[mu_offset + blk] = s;
   }

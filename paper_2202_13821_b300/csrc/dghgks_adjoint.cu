@@ -1,8 +1,8 @@
 // Adjoint (VJP) kernels of the DG-HGKS residual and their launchers.  This
-// translation unit is compiled with -Xptxas -O1: at -O3 the register
-// allocation of the large dual-number kernels falls back to 32 registers and
-// spills tens of KB per thread; at -O1 they use the register file and spill
-// little.  The forward kernels stay in dghgks_api.cu at -O3.
+// translation unit is compiled with -Xptxas -O1: at -O3 ptxas caps the face
+// VJP (one long reverse sweep per Gauss point) at 96 registers with 17 KB of
+// spills per thread; at -O1 it uses 168 registers and spills 7.6 KB.  The
+// forward kernels stay in dghgks_api.cu at -O3.
 #include "adjoint.h"
 #include "dg_adjoint.cuh"
 
@@ -25,7 +25,8 @@ cudaError_t attrs() {
 
 template <int ORDER, int NQ>
 void vjp(const double* Q, const GasPar<double>& g, const MeshDev& m, const AdjIO& io, cudaStream_t s) {
-  const dim3 fgrid((m.nx + FB - 1) / FB, m.ny, m.nz), fblock(FB * NQ * NQ);
+  constexpr int FBA = adj_fb<ORDER>();
+  const dim3 fgrid((m.nx + FBA - 1) / FBA, m.ny, m.nz), fblock(FBA * NQ * NQ);
   const size_t fblocks = (size_t)fgrid.x * fgrid.y * fgrid.z;
   const size_t fbytes = FaceAdjSmem<ORDER, NQ>::bytes;
   k_face_vjp<ORDER, NQ, 0><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 0 * fblocks);
@@ -41,6 +42,7 @@ cudaError_t adjoint_set_attrs(int order, int nq) {
   if (order == 1 && nq == 2) return attrs<1, 2>();
   if (order == 2 && nq == 2) return attrs<2, 2>();
   if (order == 2 && nq == 3) return attrs<2, 3>();
+  if (order == 3 && nq == 3) return attrs<3, 3>();
   return cudaErrorInvalidValue;
 }
 
@@ -49,6 +51,12 @@ void adjoint_vjp(int order, int nq, const double* Q, const GasPar<double>& g, co
   if (order == 1 && nq == 2) vjp<1, 2>(Q, g, m, io, s);
   else if (order == 2 && nq == 2) vjp<2, 2>(Q, g, m, io, s);
   else if (order == 2 && nq == 3) vjp<2, 3>(Q, g, m, io, s);
+  else if (order == 3 && nq == 3) vjp<3, 3>(Q, g, m, io, s);
+}
+
+long long adjoint_face_ctas(int order, int nx, int ny, int nz) {
+  const int fb = order >= 3 ? adj_fb<3>() : adj_fb<1>();
+  return (long long)((nx + fb - 1) / fb) * ny * nz;
 }
 
 void adjoint_mu_sum(const double* part, long long n, double* acc, cudaStream_t s) {
@@ -60,6 +68,7 @@ void adjoint_ek_vjp(int order, int nq, const double* Q, const MeshDev& m, double
   if (order == 1 && nq == 2) k_ek_vjp<1, 2><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, m, scale, out);
   else if (order == 2 && nq == 2) k_ek_vjp<2, 2><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, m, scale, out);
   else if (order == 2 && nq == 3) k_ek_vjp<2, 3><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, m, scale, out);
+  else if (order == 3 && nq == 3) k_ek_vjp<3, 3><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, m, scale, out);
 }
 
 }  // namespace dghgks
