@@ -748,6 +748,61 @@ __global__ void __launch_bounds__(RED_THREADS) k_totals_part(const double* __res
   block_reduce_store<5>(acc, part);
 }
 
+// Values at the NQ^3 tensor Gauss points of a modal polynomial (coefficients
+// co, the P_k Legendre basis) by sum factorisation: contract x, then y, then z
+// (q[i][j][k] at (x_i, y_j, z_k)); zero and unit basis factors fold away.
+template <int ORDER, int NQ>
+__device__ __forceinline__ void tensor_points(const double (&co)[n_modes(ORDER)], double (&q)[NQ][NQ][NQ]) {
+  constexpr int NM = n_modes(ORDER);
+  double t1[ORDER + 1][ORDER + 1][NQ];  // [b][c][i]: sum over a
+#pragma unroll
+  for (int b = 0; b <= ORDER; ++b)
+#pragma unroll
+    for (int c = 0; c <= ORDER; ++c)
+#pragma unroll
+      for (int i = 0; i < NQ; ++i) t1[b][c][i] = 0.0;
+#pragma unroll
+  for (int mm = 0; mm < NM; ++mm)
+#pragma unroll
+    for (int i = 0; i < NQ; ++i)
+      t1[mode_exp(mm, 1)][mode_exp(mm, 2)][i] += co[mm] * leg<double>(mode_exp(mm, 0), gauss_x(NQ, i));
+  double t2[ORDER + 1][NQ][NQ];  // [c][i][j]: sum over b
+#pragma unroll
+  for (int c = 0; c <= ORDER; ++c)
+#pragma unroll
+    for (int i = 0; i < NQ; ++i)
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) {
+        double s = 0.0;
+#pragma unroll
+        for (int b = 0; b + c <= ORDER; ++b) s += t1[b][c][i] * leg<double>(b, gauss_x(NQ, j));
+        t2[c][i][j] = s;
+      }
+#pragma unroll
+  for (int i = 0; i < NQ; ++i)
+#pragma unroll
+    for (int j = 0; j < NQ; ++j)
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c <= ORDER; ++c) s += t2[c][i][j] * leg<double>(c, gauss_x(NQ, k));
+        q[i][j][k] = s;
+      }
+}
+
+// 1/x in FP64 for a density: FP32 reciprocal estimate refined by two
+// Newton-Raphson steps r <- r + r (1 - x r) (quadratic convergence: the
+// seed's 2^-23 relative error falls below FP64 rounding); outside the FP32
+// normal range, the division.
+__device__ __forceinline__ double recip64(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
+
 template <int ORDER, int NQ>
 __global__ void __launch_bounds__(RED_THREADS) k_ek_part(const double* __restrict__ Q, const MeshDev m,
                                                          double* __restrict__ part) {
@@ -756,28 +811,36 @@ __global__ void __launch_bounds__(RED_THREADS) k_ek_part(const double* __restric
   double acc[1] = {0};
   for (long long c = (long long)blockIdx.x * RED_THREADS + threadIdx.x; c < nc; c += (long long)gridDim.x * RED_THREADS) {
     const double wc = cell_weight(m, c);
-    double co[4][NM];
+    double co[NM], rho[NQ][NQ][NQ], mom[NQ][NQ][NQ], m2[NQ][NQ][NQ];
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
-#pragma unroll
-      for (int mm = 0; mm < NM; ++mm) co[v][mm] = Q[(size_t)(v * NM + mm) * nc + c];
+    for (int mm = 0; mm < NM; ++mm) co[mm] = Q[(size_t)mm * nc + c];
+    tensor_points<ORDER, NQ>(co, rho);
 #pragma unroll
     for (int a = 0; a < NQ; ++a)
 #pragma unroll
       for (int b = 0; b < NQ; ++b)
 #pragma unroll
-        for (int cz = 0; cz < NQ; ++cz) {
-          double qv[4] = {0, 0, 0, 0};
+        for (int cz = 0; cz < NQ; ++cz) m2[a][b][cz] = 0.0;
 #pragma unroll
-          for (int mm = 0; mm < NM; ++mm) {
-            const double B = leg<double>(mode_exp(mm, 0), gauss_x(NQ, a)) * leg<double>(mode_exp(mm, 1), gauss_x(NQ, b)) *
-                             leg<double>(mode_exp(mm, 2), gauss_x(NQ, cz));
+    for (int v = 1; v < 4; ++v) {
 #pragma unroll
-            for (int v = 0; v < 4; ++v) qv[v] += co[v][mm] * B;
-          }
-          acc[0] += wc * (gauss_w(NQ, a) * gauss_w(NQ, b) * gauss_w(NQ, cz) * 0.5 *
-                          (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]) / qv[0]);
-        }
+      for (int mm = 0; mm < NM; ++mm) co[mm] = Q[(size_t)(v * NM + mm) * nc + c];
+      tensor_points<ORDER, NQ>(co, mom);
+#pragma unroll
+      for (int a = 0; a < NQ; ++a)
+#pragma unroll
+        for (int b = 0; b < NQ; ++b)
+#pragma unroll
+          for (int cz = 0; cz < NQ; ++cz) m2[a][b][cz] += mom[a][b][cz] * mom[a][b][cz];
+    }
+#pragma unroll
+    for (int a = 0; a < NQ; ++a)
+#pragma unroll
+      for (int b = 0; b < NQ; ++b)
+#pragma unroll
+        for (int cz = 0; cz < NQ; ++cz)
+          acc[0] += wc * (gauss_w(NQ, a) * gauss_w(NQ, b) * gauss_w(NQ, cz) * 0.5 * m2[a][b][cz] *
+                          recip64(rho[a][b][cz]));
   }
   block_reduce_store<1>(acc, part);
 }
