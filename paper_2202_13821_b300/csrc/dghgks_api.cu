@@ -44,6 +44,8 @@ struct dghgks_ctx {
   double* red = nullptr;   // reduction results (device)
   double* red_host = nullptr;  // pinned
   double* Qdev = nullptr;      // device state for dghgks_run_host
+  cudaStream_t ek_stream = nullptr;  // dghgks_run_host: E_k of step n beside step n+1
+  cudaEvent_t ev_q = nullptr, ev_ek = nullptr;
   // adjoint scratch (FP64 contexts, allocated on first use)
   double* adjH = nullptr;      // face cotangents [3][2][5 N_m][cells]
   double* adjLam = nullptr;    // lambda* (state size)
@@ -315,7 +317,7 @@ int read_flag(dghgks_ctx* c, cudaStream_t s) {
 
 extern "C" {
 
-static void enqueue_step(dghgks_ctx* c, double* Q, double dt, cudaStream_t s);
+static void enqueue_step(dghgks_ctx* c, double* Q, double dt, cudaStream_t s, cudaEvent_t before_write);
 
 int dghgks_gauss_rule(int n, double* x, double* w) {
   if (n < 1 || n > 5 || !x || !w) return DGHGKS_EARG;
@@ -453,6 +455,9 @@ void dghgks_destroy(dghgks_ctx* c) {
   cudaFree(c->adjMu);
   cudaFree(c->geo64);
   cudaFree(c->geo32);
+  if (c->ev_q) cudaEventDestroy(c->ev_q);
+  if (c->ev_ek) cudaEventDestroy(c->ev_ek);
+  if (c->ek_stream) cudaStreamDestroy(c->ek_stream);
   if (c->red_host) cudaFreeHost(c->red_host);
   delete c;
 }
@@ -486,15 +491,18 @@ int dghgks_step(dghgks_ctx* c, double* Q, double dt, void* stream) {
   if (!Q) return fail(c, DGHGKS_EARG, "Q is NULL");
   if (!(dt > 0)) return fail(c, DGHGKS_EARG, "dt must be > 0");
   // stage 1 at Q^n, stage 2 at Q* (same dt for the flux fit; only L_t(Q*) enters)
-  enqueue_step(c, Q, dt, static_cast<cudaStream_t>(stream));
+  enqueue_step(c, Q, dt, static_cast<cudaStream_t>(stream), nullptr);
   return after_launch(c, "step launch");
 }
 
-// Enqueue the 8 launches of one S2O4 step on s.
-static void enqueue_step(dghgks_ctx* c, double* Q, double dt, cudaStream_t s) {
+// Enqueue the 8 launches of one S2O4 step on s.  before_write (may be null): an event that the stage-2
+// cell kernel, the only writer of Q, waits for (readers of Q^n on another
+// stream).
+static void enqueue_step(dghgks_ctx* c, double* Q, double dt, cudaStream_t s, cudaEvent_t before_write) {
   c->ops->faces(c, Q, false, dt, s);
   c->ops->cell(c, MODE_STAGE1, Q, nullptr, nullptr, dt, s);  // Q*, inc
   c->ops->faces(c, c->Qs, true, dt, s);
+  if (before_write) cudaStreamWaitEvent(s, before_write, 0);
   c->ops->cell(c, MODE_STAGE2, Q, nullptr, nullptr, dt, s);  // Q += inc + dt^2/3 L_t(Q*)
 }
 
@@ -515,7 +523,7 @@ int dghgks_steps(dghgks_ctx* c, double* Q, double dt, int nsteps, void* stream) 
     cudaGraph_t graph = nullptr;
     if (int rc = cuda_check(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "capture"))
       return rc;
-    enqueue_step(c, Q, dt, c->cap_stream);
+    enqueue_step(c, Q, dt, c->cap_stream, nullptr);
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
     c->prof = prof;
     c->launches = launches;
@@ -634,16 +642,31 @@ int dghgks_run_host(dghgks_ctx* c, double* Q_host, double dt, int nsteps, double
     if (int rc = cuda_check(c, cudaMalloc(&c->Qdev, state), "cudaMalloc(run state)")) return rc;
   if (int rc = cuda_check(c, cudaMemcpyAsync(c->Qdev, Q_host, state, cudaMemcpyHostToDevice, s), "H2D state"))
     return rc;
+  // E_k of step n runs on a second stream while step n+1 computes: both only
+  // read Q^{n+1} until step n+1's stage-2 cell kernel, which waits for it.
+  if (ek_host && !c->ek_stream) {
+    int rc = cuda_check(c, cudaStreamCreateWithFlags(&c->ek_stream, cudaStreamNonBlocking), "E_k stream");
+    if (!rc) rc = cuda_check(c, cudaEventCreateWithFlags(&c->ev_q, cudaEventDisableTiming), "event");
+    if (!rc) rc = cuda_check(c, cudaEventCreateWithFlags(&c->ev_ek, cudaEventDisableTiming), "event");
+    if (rc) return rc;
+  }
+  bool ek_pending = false;
   for (int n = 0; n < nsteps; ++n) {
-    if (int rc = dghgks_step(c, c->Qdev, dt, stream)) return rc;
+    enqueue_step(c, c->Qdev, dt, s, ek_pending ? c->ev_ek : nullptr);
+    if (int rc = after_launch(c, "step launch")) return rc;
     if (ek_host) {
-      if (int rc = enqueue_ek(c, c->Qdev, rho0, c->red + (n % 8), s)) return rc;
+      cudaStream_t e = c->ek_stream;
+      if (int rc = cuda_check(c, cudaEventRecord(c->ev_q, s), "event")) return rc;
+      if (int rc = cuda_check(c, cudaStreamWaitEvent(e, c->ev_q, 0), "event")) return rc;
+      if (int rc = enqueue_ek(c, c->Qdev, rho0, c->red + (n % 8), e)) return rc;
       if (int rc = cuda_check(c, cudaMemcpyAsync(c->red_host + (n % 8), c->red + (n % 8), sizeof(double),
-                                                 cudaMemcpyDeviceToHost, s),
+                                                 cudaMemcpyDeviceToHost, e),
                               "D2H E_k"))
         return rc;
+      if (int rc = cuda_check(c, cudaEventRecord(c->ev_ek, e), "event")) return rc;
+      ek_pending = true;
       if (n % 8 == 7 || n == nsteps - 1) {
-        if (int rc = cuda_check(c, cudaStreamSynchronize(s), "E_k sync")) return rc;
+        if (int rc = cuda_check(c, cudaStreamSynchronize(e), "E_k sync")) return rc;
         for (int m = n - (n % 8); m <= n; ++m) ek_host[m] = c->red_host[m % 8];
       }
     }

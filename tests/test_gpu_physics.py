@@ -153,6 +153,28 @@ def test_deterministic_and_graph_replay_bitwise(torch, api):
         assert torch.equal(D, E)
 
 
+def test_run_host_matches_device_steps(torch, api):
+    """dghgks_run_host (host state in and out, E_k of each step on a second stream beside the next
+    step) gives bitwise the state and E_k history of device steps with E_k after each."""
+    from paper_2202_13821_b300 import inputs
+
+    n = (24, 20, 16)
+    for prec in (0, 1):
+        s = api.Solver(n, **TGV, order=2, mu=1 / 1600, Pr=0.72, precision=prec)
+        Q0 = inputs.tgv_state(n, 2, perturb=1e-3, device="cuda")
+        Qd = Q0.clone()
+        ek_dev = []
+        for _ in range(11):
+            s.step(Qd, 3e-3)
+            ek_dev.append(s.kinetic_energy(Qd))
+        host = torch.empty(Q0.shape, dtype=torch.float64, pin_memory=True)
+        host.copy_(Q0)
+        ek_host = s.run_host(host.numpy(), 3e-3, 11)
+        s.status()
+        assert torch.equal(host.cuda(), Qd)
+        assert np.array_equal(ek_host, np.array(ek_dev))
+
+
 def test_graph_replay_follows_set_mu(torch, api):
     """dghgks_steps after dghgks_set_mu uses the new viscosity (the graph is captured again)."""
     from paper_2202_13821_b300 import inputs
