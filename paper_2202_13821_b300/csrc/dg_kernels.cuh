@@ -602,9 +602,10 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       }
     } else {
       // ---- a cell spans GW warps: per-warp butterflies over the modes n >= 1,
-      // partial sums through shared memory, then the epilogue over the CTA ----
+      // partial sums through shared memory, then the epilogue over the CTA
+      // (the stage-2 pass reduces the F_t kind only) ----
   #pragma unroll
-      for (int kind = 0; kind < 2; ++kind) {
+      for (int kind = MODE == MODE_STAGE2 ? 1 : 0; kind < 2; ++kind) {
   #pragma unroll
         for (int c0 = 0; c0 < NOP; c0 += PG) {
           R val[PG];
