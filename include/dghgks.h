@@ -131,18 +131,23 @@ int dghgks_steps(dghgks_ctx* ctx, double* Q, double dt, int nsteps, void* stream
 
 /* nsteps S2O4 steps on a HOST state (pinned or pageable): copies Q_host to
  * the device, steps, and copies the result back; if ek_host is not NULL it
- * receives E_k (as dghgks_kinetic_energy with rho0) after every step.
- * Synchronises.  Allocates one device state buffer on first use. */
+ * receives E_k (as dghgks_kinetic_energy with rho0) after every step (host
+ * memory, nsteps doubles).  The E_k of step n runs on a second, library-owned
+ * stream beside step n+1, whose state update waits for it; results are
+ * bitwise those of dghgks_step + dghgks_kinetic_energy.  Synchronises.
+ * Allocates one device state buffer (and the second stream) on first use. */
 int dghgks_run_host(dghgks_ctx* ctx, double* Q_host, double dt, int nsteps, double rho0, double* ek_host,
                     void* stream);
 
-/* Conserved totals sum_cells |K| Q_(var, mode 0), var = 0..4, in FP64.
+/* Conserved totals sum_cells |K| Q_(var, mode 0), var = 0..4, in FP64
+ * (|K| per cell on a rectilinear mesh).
  * Synchronises; out is host memory (5 doubles). */
 int dghgks_totals(dghgks_ctx* ctx, const double* Q, double* out, void* stream);
 
 /* Volume-averaged kinetic energy E_k = 1/(rho0 |Omega|) int rho|U|^2/2
- * (Sec. 5.3), by the n_q^3 cell Gauss rule, in FP64.  Synchronises; Ek is
- * host memory. */
+ * (Sec. 5.3), by the n_q^3 cell Gauss rule, in FP64 (point values by sum
+ * factorisation; 1/rho from an FP32 estimate and two Newton steps, exact to
+ * FP64 rounding).  Synchronises; Ek is host memory. */
 int dghgks_kinetic_energy(dghgks_ctx* ctx, const double* Q, double rho0, double* Ek, void* stream);
 
 /* Enstrophy-based dissipation rate (Sec. 5.3):
