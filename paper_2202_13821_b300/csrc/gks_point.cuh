@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <utility>
 
 // Point functions compile for the device and, for the operation counter, for
 // the host with a counting scalar type.
@@ -263,6 +264,208 @@ DG_HD void fit_weights(R tau, R dt, R inv_dt, R wF[6], R wFt[6]) {
 }
 
 // ---------------------------------------------------------------------------
+// Moments in a frame that moves with the Maxwellian.
+//
+// With c = u - s for a shift s, psi = S_s psi' where psi' = (1, c_u, c_v,
+// c_w, (|c|^2 + xi^2)/2) and
+//   S_s m' = (m'0, m'1 + s_u m'0, m'2 + s_v m'0, m'3 + s_w m'0,
+//             m'4 + s . m'_{1..3} + |s|^2/2 m'0),
+// so a . psi = (S_s^T a) . psi' and <phi psi> = S_s <phi psi'>; S_a S_b =
+// S_{a+b}.  The tangential components are always centred on the Maxwellian's
+// velocity (s_v = V, s_w = W); the normal one is centred too (s_u = U, full
+// space, CU = true) or not (s_u = 0, the half-space moments of one side of an
+// interface, CU = false).  Central moments of odd order of a full-space
+// Gaussian vanish, so every moment product containing one is dropped at
+// compile time: the 5 x 5 moment matrices <c^ABC psi' psi'^T> keep 11, 6 or
+// 2 of their 25 entries.  The results are those of the lab-frame formulas;
+// only the rounding order differs.
+// ---------------------------------------------------------------------------
+template <class R>
+struct CTab {
+  R u[7];        // <c_u^n>: the raw half-space moments (CU = false)
+  R c2, c4, c6;  // central moments of a full-space component: h, 3 h^2, 15 h^3
+  R xi2, xi4;    // <xi^2>, <xi^4>
+};
+
+template <class R>
+DG_HD void cent_table(R h, R K, CTab<R>& t) {
+  t.c2 = h;
+  t.c4 = R(3) * h * h;
+  t.c6 = R(15) * h * h * h;
+  t.xi2 = K * h;
+  t.xi4 = K * (K + R(2)) * h * h;
+}
+
+template <bool CU, int A, int B, int C>
+constexpr bool cm_zero() {
+  return (B % 2) || (C % 2) || (CU && (A % 2));
+}
+template <int N, class R>
+DG_HD R cm_c(const CTab<R>& t) {  // central moment of even order N of a full-space component
+  static_assert(N % 2 == 0 && N <= 6, "central moment out of table");
+  if constexpr (N == 0) return R(1);
+  else if constexpr (N == 2) return t.c2;
+  else if constexpr (N == 4) return t.c4;
+  else return t.c6;
+}
+// <c_u^A c_v^B c_w^C>, for a non-vanishing moment only
+template <bool CU, int A, int B, int C, class R>
+DG_HD R cm(const CTab<R>& t) {
+  static_assert(!cm_zero<CU, A, B, C>(), "vanishing moment");
+  static_assert(A <= 6, "moment power out of table");
+  R x;
+  if constexpr (CU) x = cm_c<A>(t);
+  else x = t.u[A];
+  if constexpr (B > 0) x = x * cm_c<B>(t);
+  if constexpr (C > 0) x = x * cm_c<C>(t);
+  return x;
+}
+// <c^ABC psi'_4> and <c^ABC psi'_4^2> (same parity as <c^ABC>)
+template <bool CU, int A, int B, int C, class R>
+DG_HD R cm5(const CTab<R>& t) {
+  return R(0.5) * (cm<CU, A + 2, B, C>(t) + cm<CU, A, B + 2, C>(t) + cm<CU, A, B, C + 2>(t) + t.xi2 * cm<CU, A, B, C>(t));
+}
+template <bool CU, int A, int B, int C, class R>
+DG_HD R cm55(const CTab<R>& t) {
+  return R(0.25) * (cm<CU, A + 4, B, C>(t) + cm<CU, A, B + 4, C>(t) + cm<CU, A, B, C + 4>(t) +
+                    R(2) * (cm<CU, A + 2, B + 2, C>(t) + cm<CU, A + 2, B, C + 2>(t) + cm<CU, A, B + 2, C + 2>(t)) +
+                    R(2) * t.xi2 * (cm<CU, A + 2, B, C>(t) + cm<CU, A, B + 2, C>(t) + cm<CU, A, B, C + 2>(t)) +
+                    t.xi4 * cm<CU, A, B, C>(t));
+}
+// <c^ABC psi'_J psi'_K> (psi'_0 = 1, psi'_{1,2,3} = c_{u,v,w}, psi'_4 even)
+template <bool CU, int J, int K, int A, int B, int C>
+constexpr bool ent_zero() {
+  return cm_zero<CU, A + (J == 1) + (K == 1), B + (J == 2) + (K == 2), C + (J == 3) + (K == 3)>();
+}
+template <bool CU, int J, int K, int A, int B, int C, class R>
+DG_HD R ent(const CTab<R>& t) {
+  if constexpr (J == 4 && K == 4) return cm55<CU, A, B, C>(t);
+  else if constexpr (J == 4) return cm5<CU, A + (K == 1), B + (K == 2), C + (K == 3)>(t);
+  else if constexpr (K == 4) return cm5<CU, A + (J == 1), B + (J == 2), C + (J == 3)>(t);
+  else return cm<CU, A + (J == 1) + (K == 1), B + (J == 2) + (K == 2), C + (J == 3) + (K == 3)>(t);
+}
+
+template <bool CU, int A, int B, int C, int K, int J, class R>
+DG_HD void cmom_a_term(const CTab<R>& t, const R a[5], R out[5]) {
+  if constexpr (!ent_zero<CU, J, K, A, B, C>()) out[K] += a[J] * ent<CU, J, K, A, B, C>(t);
+}
+template <bool CU, int A, int B, int C, class R, int... I>
+DG_HD void cmom_a_seq(const CTab<R>& t, const R a[5], R out[5], std::integer_sequence<int, I...>) {
+  (cmom_a_term<CU, A, B, C, I / 5, I % 5>(t, a, out), ...);
+}
+// out += <c^ABC (a . psi') psi'>
+template <bool CU, int A, int B, int C, class R>
+DG_HD void cmom_a(const CTab<R>& t, const R a[5], R out[5]) {
+  cmom_a_seq<CU, A, B, C>(t, a, out, std::make_integer_sequence<int, 25>{});
+}
+// out += s <c^ABC psi'>
+template <bool CU, int A, int B, int C, class R>
+DG_HD void cmom_psi(const CTab<R>& t, R s, R out[5]) {
+  if constexpr (!ent_zero<CU, 0, 0, A, B, C>()) out[0] += s * ent<CU, 0, 0, A, B, C>(t);
+  if constexpr (!ent_zero<CU, 0, 1, A, B, C>()) out[1] += s * ent<CU, 0, 1, A, B, C>(t);
+  if constexpr (!ent_zero<CU, 0, 2, A, B, C>()) out[2] += s * ent<CU, 0, 2, A, B, C>(t);
+  if constexpr (!ent_zero<CU, 0, 3, A, B, C>()) out[3] += s * ent<CU, 0, 3, A, B, C>(t);
+  if constexpr (!ent_zero<CU, 0, 4, A, B, C>()) out[4] += s * ent<CU, 0, 4, A, B, C>(t);
+}
+// out += <c_D (a . psi') psi'>, D = 0, 1, 2 (u, v, w)
+template <bool CU, int D, class R>
+DG_HD void cmom_a_e(const CTab<R>& t, const R a[5], R out[5]) {
+  cmom_a<CU, D == 0, D == 1, D == 2>(t, a, out);
+}
+// out += <c_D c_E (a . psi') psi'>
+template <bool CU, int D, int E, class R>
+DG_HD void cmom_a_ee(const CTab<R>& t, const R a[5], R out[5]) {
+  cmom_a<CU, (D == 0) + (E == 0), (D == 1) + (E == 1), (D == 2) + (E == 2)>(t, a, out);
+}
+
+// m'' = S_{-s} m (lab -> frame centred on s = (U, V, W)); hs2 = |s|^2 / 2
+template <class R>
+DG_HD void to_centred(const R m[5], R U, R V, R W, R hs2, R out[5]) {
+  out[0] = m[0];
+  out[1] = m[1] - U * m[0];
+  out[2] = m[2] - V * m[0];
+  out[3] = m[3] - W * m[0];
+  out[4] = m[4] - U * m[1] - V * m[2] - W * m[3] + hs2 * m[0];
+}
+// out += S_s m' (frame centred on s -> lab); SU = false for s_u = 0
+template <bool SU, class R>
+DG_HD void add_uncentred(const R mp[5], R U, R V, R W, R hs2, R out[5]) {
+  out[0] += mp[0];
+  if constexpr (SU) {
+    out[1] += mp[1] + U * mp[0];
+    out[4] += mp[4] + U * mp[1] + V * mp[2] + W * mp[3] + hs2 * mp[0];
+  } else {
+    out[1] += mp[1];
+    out[4] += mp[4] + V * mp[2] + W * mp[3] + hs2 * mp[0];
+  }
+  out[2] += mp[2] + V * mp[0];
+  out[3] += mp[3] + W * mp[0];
+}
+
+// Closed-form solution of <(a . psi'') psi''> = b for the full-space
+// Maxwellian in its own frame: the moment matrix has <1> = 1, <c_i^2> = h,
+// <psi''_4> = (K+3) h / 2 = e1 and <psi''_4^2> - e1^2 = (K+3) h^2 / 2, so
+// a_i = b_i / h, a_4 = (b_4 - e1 b_0) 2 / ((K+3) h^2), a_0 = b_0 - e1 a_4.
+template <class R>
+struct CSolve {
+  R e1;    // <psi''_4>
+  R k4;    // 2 / ((K+3) h^2) = 8 lam^2 / (K+3)
+  R tlam;  // 1 / h = 2 lam
+};
+template <class R>
+DG_HD void centred_solver(R lam, R h, R K, CSolve<R>& cs) {
+  cs.e1 = R(0.5) * (K + R(3)) * h;
+  cs.k4 = fdiv(R(8) * lam * lam, K + R(3));
+  cs.tlam = R(2) * lam;
+}
+template <class R>
+DG_HD void centred_solve(const CSolve<R>& cs, const R b[5], R a[5]) {
+  a[4] = cs.k4 * (b[4] - cs.e1 * b[0]);
+  a[1] = cs.tlam * b[1];
+  a[2] = cs.tlam * b[2];
+  a[3] = cs.tlam * b[3];
+  a[0] = b[0] - cs.e1 * a[4];
+}
+
+// Coefficients in the frame centred on s -> in the frame centred on s + (d, 0, 0)
+// (c_u = c_u' + d): a' = S_{(d,0,0)}^T a, in place
+template <class R>
+DG_HD void coef_shift_u(R a[5], R d) {
+  a[0] = a[0] + d * a[1] + R(0.5) * d * d * a[4];
+  a[1] = a[1] + d * a[4];
+}
+
+// Slopes of one state in its own frame: a''_i from the derivatives dq_i
+// (b_i = dq_i / rho taken to the centred frame), the centred right-hand sides
+// b''_i, and the compatibility condition <A psi> = -<(a . u) psi> for A'',
+// whose right-hand side -Wau'' is returned too (u_i = c_i + U_i, and
+// <(a''_i . psi'') psi''> = b''_i).
+template <class R>
+DG_HD void centred_slopes(const Prim<R>& p, R ir, R hs2, const CSolve<R>& cs, const CTab<R>& t, const R dq[3][5],
+                          R a[3][5], R Wau[5], R A[5]) {
+  const R Uc[3] = {p.U, p.V, p.W};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) Wau[k] = R(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R b[5], bc[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) b[k] = dq[i][k] * ir;
+    to_centred(b, p.U, p.V, p.W, hs2, bc);
+    centred_solve(cs, bc, a[i]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Wau[k] += Uc[i] * bc[k];
+  }
+  cmom_a_e<true, 0>(t, a[0], Wau);
+  cmom_a_e<true, 1>(t, a[1], Wau);
+  cmom_a_e<true, 2>(t, a[2], Wau);
+  R bA[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) bA[k] = -Wau[k];
+  centred_solve(cs, bA, A);
+}
+
+// ---------------------------------------------------------------------------
 // Interface flux (local frame: component 1 = normal).  q*, dq* are the traces
 // and derivatives (n_1 = normal, n_2, n_3) of the left (u>0 upwind) and right
 // states.  Returns false if a state is not physical.
@@ -276,40 +479,73 @@ struct SideSums {
 
 // One side of the interface: SGN = +1 for the left state (its u > 0
 // half-space reaches the interface), -1 for the right state.  SGN is a runtime
-// value so that a kernel can loop over the two sides without unrolling.
+// value so that a kernel can loop over the two sides without unrolling.  The
+// slopes are solved in the state's own frame; the half-space moments are
+// taken in the frame centred on (0, V, W) and added to the sums in the lab
+// (local) frame.
 template <class R>
 DG_HD bool iface_side(int SGN, const R q[5], const R dq[3][5], const GasPar<R>& g, bool pr_fix,
                       SideSums<R>& S) {
   Prim<R> p;
   const bool ok = prim_of(q, g.gm1, p);
   const R ir = fdiv(R(1), p.rho);
-  R a[3][5];
+  const R h = fdiv(R(0.5), p.lam);
+  const R ht2 = R(0.5) * (p.V * p.V + p.W * p.W);
+  const R hs2 = R(0.5) * p.U * p.U + ht2;
+  CTab<R> t;
+  cent_table(h, g.K, t);
+  CSolve<R> cs;
+  centred_solver(p.lam, h, g.K, cs);
+  R a[3][5], Wau[5], A[5];
+  centred_slopes(p, ir, hs2, cs, t, dq, a, Wau, A);
+  // to the frame centred on (0, V, W), scaled by rho (the moments are linear in them)
+  const R r = p.rho;
+  coef_shift_u(A, -p.U);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) A[k] = r * A[k];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    R b[5];
+    coef_shift_u(a[i], -p.U);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) b[k] = dq[i][k] * ir;
-    slope_solve(p, g.K, b, a[i]);
+    for (int k = 0; k < 5; ++k) a[i][k] = r * a[i][k];
   }
-  MomTab<R> t;
-  full_table(p, g.K, t);
-  // compatibility: <A psi> = -<(a.u) psi>
-  R bA[5] = {R(0), R(0), R(0), R(0), R(0)};
-  mom_adotu_psi<0, 0>(t, a, R(-1), bA);
-  R A[5];
-  slope_solve(p, g.K, bA, A);
-  // half-space table along the normal
-  half_line(t.u, p.U, p.lam, fdiv(R(0.5), p.lam), SGN);
-  const R r = p.rho;
-  mom_psi<0, 0, 0>(t, r, S.Q0);
+  // sum_i u_i a_i with u_2 = c_v + V, u_3 = c_w + W: the shifted parts
+  R aVW[5];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) mom_a_psi<0, 0, 0>(t, a[i], r, S.dQ0[i]);
-  mom_psi<1, 0, 0>(t, r, S.V4);
-  mom_adotu_psi<0, 1>(t, a, r, S.V5);
-  mom_a_psi<1, 0, 0>(t, A, r, S.V6);
+  for (int k = 0; k < 5; ++k) aVW[k] = p.V * a[1][k] + p.W * a[2][k];
+  // half-space table along the normal
+  half_line(t.u, p.U, p.lam, h, SGN);
+  // each sum: its moments in the frame of the table, then added in the lab frame
+  R m[5] = {R(0), R(0), R(0), R(0), R(0)};
+  auto add_to = [&](R dst[5]) {
+    add_uncentred<false>(m, R(0), p.V, p.W, ht2, dst);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) m[k] = R(0);
+  };
+  cmom_psi<false, 0, 0, 0>(t, r, m);
+  add_to(S.Q0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cmom_a<false, 0, 0, 0>(t, a[i], m);
+    add_to(S.dQ0[i]);
+  }
+  cmom_psi<false, 1, 0, 0>(t, r, m);
+  add_to(S.V4);
+  cmom_a<false, 2, 0, 0>(t, a[0], m);
+  cmom_a<false, 1, 1, 0>(t, a[1], m);
+  cmom_a<false, 1, 0, 1>(t, a[2], m);
+  cmom_a<false, 1, 0, 0>(t, aVW, m);
+  add_to(S.V5);
+  cmom_a<false, 1, 0, 0>(t, A, m);
+  add_to(S.V6);
   if (pr_fix) {
-    mom_adotu_psi<0, 0>(t, a, r, S.W5);
-    mom_a_psi<0, 0, 0>(t, A, r, S.W6);
+    cmom_a<false, 1, 0, 0>(t, a[0], m);
+    cmom_a<false, 0, 1, 0>(t, a[1], m);
+    cmom_a<false, 0, 0, 1>(t, a[2], m);
+    cmom_a<false, 0, 0, 0>(t, aVW, m);
+    add_to(S.W5);
+    cmom_a<false, 0, 0, 0>(t, A, m);
+    add_to(S.W6);
   }
   return ok;
 }
@@ -330,63 +566,74 @@ DG_HD void iface_zero(SideSums<R>& S) {
 }
 
 // Equilibrium state g_0 of the interface, its slopes, tau, the time fit, and
-// the flux (local frame) from the side sums of both sides.
+// the flux (local frame) from the side sums of both sides; the g_0 terms are
+// formed in the frame of g_0.
 template <class R>
 DG_HD bool iface_finish(const SideSums<R>& S, const GasPar<R>& g, R F[5], R Ft[5]) {
   const bool pr_fix = (g.pr_fix != R(0));
   Prim<R> p0;
   const bool ok = prim_of(S.Q0, g.gm1, p0);
   const R ir0 = fdiv(R(1), p0.rho);
-  R ab[3][5];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    R b[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) b[k] = S.dQ0[i][k] * ir0;
-    slope_solve(p0, g.K, b, ab[i]);
-  }
-  MomTab<R> t0;
-  full_table(p0, g.K, t0);
-  R Wab[5] = {R(0), R(0), R(0), R(0), R(0)};
-  mom_adotu_psi<0, 0>(t0, ab, R(1), Wab);  // <(abar.u) psi>
-  R bA[5], Ab[5];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) bA[k] = -Wab[k];
-  slope_solve(p0, g.K, bA, Ab);
+  const R h = fdiv(R(0.5), p0.lam);
+  const R U = p0.U, V = p0.V, W = p0.W;
+  const R hs2 = R(0.5) * (U * U + V * V + W * W);
+  CTab<R> t0;
+  cent_table(h, g.K, t0);
+  CSolve<R> cs;
+  centred_solver(p0.lam, h, g.K, cs);
+  R ab[3][5], Wab[5], Ab[5];  // abar_i, <(abar . u) psi>, Abar (frame of g_0)
+  centred_slopes(p0, ir0, hs2, cs, t0, S.dQ0, ab, Wab, Ab);
 
   // collision time and fit weights
   const R tau = fdiv(g.mu * R(2) * p0.lam, p0.rho) + g.tau_add;  // mu / p_0 + tau_eps dt
   R wF[6], wFt[6];
   fit_weights(tau, g.dt, g.inv_dt, wF, wFt);
 
-  R V1[5] = {R(0), R(0), R(0), R(0), R(0)}, V2[5] = {R(0), R(0), R(0), R(0), R(0)},
-    V3[5] = {R(0), R(0), R(0), R(0), R(0)};
-  const R r0 = p0.rho;
-  mom_psi<1, 0, 0>(t0, r0, V1);
-  mom_adotu_psi<0, 1>(t0, ab, r0, V2);
-  mom_a_psi<1, 0, 0>(t0, Ab, r0, V3);
+  // g_0 terms (per unit density): V1 = <u psi>, V2 = <u (abar . u) psi>,
+  // V3 = <u Abar psi>, with u = c_u + U, u_i = c_i + U_i
+  R V1[5] = {R(0), R(0), R(0), R(0), R(0)}, V2[5], V3[5], aU[5];
+  cmom_psi<true, 0, 0, 0>(t0, U, V1);
+  cmom_psi<true, 1, 0, 0>(t0, R(1), V1);
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    F[k] = wF[0] * V1[k] + wF[1] * V2[k] + wF[2] * V3[k] + wF[3] * S.V4[k] + wF[4] * S.V5[k] + wF[5] * S.V6[k];
-    Ft[k] = wFt[0] * V1[k] + wFt[1] * V2[k] + wFt[2] * V3[k] + wFt[3] * S.V4[k] + wFt[4] * S.V5[k] +
-            wFt[5] * S.V6[k];
+    aU[k] = U * ab[0][k] + V * ab[1][k] + W * ab[2][k];
+    V2[k] = U * Wab[k];
+    V3[k] = -U * Wab[k];
+  }
+  cmom_a_ee<true, 0, 0>(t0, ab[0], V2);
+  cmom_a_ee<true, 0, 1>(t0, ab[1], V2);
+  cmom_a_ee<true, 0, 2>(t0, ab[2], V2);
+  cmom_a_e<true, 0>(t0, aU, V2);
+  cmom_a_e<true, 0>(t0, Ab, V3);
+  // free-transport sums in the frame of g_0
+  R V4[5], V5[5], V6[5];
+  to_centred(S.V4, U, V, W, hs2, V4);
+  to_centred(S.V5, U, V, W, hs2, V5);
+  to_centred(S.V6, U, V, W, hs2, V6);
+  const R r0 = p0.rho;
+  R Fc[5], Ftc[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    Fc[k] = r0 * (wF[0] * V1[k] + wF[1] * V2[k] + wF[2] * V3[k]) + wF[3] * V4[k] + wF[4] * V5[k] + wF[5] * V6[k];
+    Ftc[k] = r0 * (wFt[0] * V1[k] + wFt[1] * V2[k] + wFt[2] * V3[k]) + wFt[3] * V4[k] + wFt[4] * V5[k] +
+             wFt[5] * V6[k];
   }
   if (pr_fix) {
-    // heat moments of terms 2..6 about U_0 (term 1, g_0 itself, carries none)
-    R W2[5], W3[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      W2[k] = r0 * Wab[k];
-      W3[k] = -r0 * Wab[k];
-    }
-    const R H2 = heat_of(V2, W2, p0.U, p0.V, p0.W, 0);
-    const R H3 = heat_of(V3, W3, p0.U, p0.V, p0.W, 0);
-    const R H4 = heat_of(S.V4, S.Q0, p0.U, p0.V, p0.W, 0);
-    const R H5 = heat_of(S.V5, S.W5, p0.U, p0.V, p0.W, 0);
-    const R H6 = heat_of(S.V6, S.W6, p0.U, p0.V, p0.W, 0);
-    F[4] += g.pr_fix * (wF[1] * H2 + wF[2] * H3 + wF[3] * H4 + wF[4] * H5 + wF[5] * H6);
-    Ft[4] += g.pr_fix * (wFt[1] * H2 + wFt[2] * H3 + wFt[3] * H4 + wFt[4] * H5 + wFt[5] * H6);
+    // heat moments 1/2 <c_u (|c|^2 + xi^2) phi> = <c_u psi''_4 phi> of terms 2..6 (term 1, g_0
+    // itself, carries none): component 4 of <u psi'' phi> - U <psi'' phi>
+    auto c4 = [&](const R m[5]) { return m[4] - U * m[1] - V * m[2] - W * m[3] + hs2 * m[0]; };
+    const R H2 = r0 * (V2[4] - U * Wab[4]);
+    const R H3 = r0 * (V3[4] + U * Wab[4]);
+    const R H4 = V4[4] - U * c4(S.Q0);
+    const R H5 = V5[4] - U * c4(S.W5);
+    const R H6 = V6[4] - U * c4(S.W6);
+    Fc[4] += g.pr_fix * (wF[1] * H2 + wF[2] * H3 + wF[3] * H4 + wF[4] * H5 + wF[5] * H6);
+    Ftc[4] += g.pr_fix * (wFt[1] * H2 + wFt[2] * H3 + wFt[3] * H4 + wFt[4] * H5 + wFt[5] * H6);
   }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) F[k] = Ft[k] = R(0);
+  add_uncentred<true>(Fc, U, V, W, hs2, F);
+  add_uncentred<true>(Ftc, U, V, W, hs2, Ft);
   return ok;
 }
 
@@ -402,54 +649,46 @@ DG_HD bool iface_flux(const R qL[5], const R dqL[3][5], const R qR[5], const R d
 }
 
 // ---------------------------------------------------------------------------
-// Interior flux of Eq. (flux-2) in the global frame: F[d][k], Ft[d][k].
+// Interior flux of Eq. (flux-2) in the global frame: F[d][k], Ft[d][k], formed
+// in the frame of the cell-point Maxwellian:
+//   m0 = <u_d psi>, m1 = sum_i <u_d u_i (a_i . psi) psi>, m2 = <u_d (A . psi) psi>,
+//   F = rho (m0 - tau (m1 + m2)), F_t = rho m2.
 // ---------------------------------------------------------------------------
 template <int D, class R>
-DG_HD void interior_dir(const MomTab<R>& t, const Prim<R>& p, const R a[3][5], const R A[5],
-                                             const R Wau[5], R tau, const GasPar<R>& g, R F[5], R Ft[5]) {
-  R m0[5] = {R(0), R(0), R(0), R(0), R(0)}, m1[5] = {R(0), R(0), R(0), R(0), R(0)},
-    m2[5] = {R(0), R(0), R(0), R(0), R(0)};
-  mom_ud_psi<D>(t, R(1), m0);
-  mom_adotu_psi<D, 1>(t, a, R(1), m1);
-  mom_ud_a_psi<D>(t, A, R(1), m2);
+DG_HD void interior_dir(const CTab<R>& t, const Prim<R>& p, R hs2, const R a[3][5], const R aU[5], const R A[5],
+                        const R Wau[5], R tau, const GasPar<R>& g, R F[5], R Ft[5]) {
+  const R Ud = (D == 0) ? p.U : (D == 1) ? p.V : p.W;
+  R m0[5] = {R(0), R(0), R(0), R(0), R(0)}, m1[5], m2[5];
+  cmom_psi<true, 0, 0, 0>(t, Ud, m0);
+  cmom_psi<true, D == 0, D == 1, D == 2>(t, R(1), m0);
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    F[k] = p.rho * (m0[k] - tau * (m1[k] + m2[k]));
-    Ft[k] = p.rho * m2[k];
+    m1[k] = Ud * Wau[k];
+    m2[k] = -Ud * Wau[k];
+  }
+  cmom_a_ee<true, D, 0>(t, a[0], m1);
+  cmom_a_ee<true, D, 1>(t, a[1], m1);
+  cmom_a_ee<true, D, 2>(t, a[2], m1);
+  cmom_a_e<true, D>(t, aU, m1);
+  cmom_a_e<true, D>(t, A, m2);
+  R Fc[5], Ftc[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    Fc[k] = p.rho * (m0[k] - tau * (m1[k] + m2[k]));
+    Ftc[k] = p.rho * m2[k];
   }
   if (g.pr_fix != R(0)) {
-    // velocity ordered with the flux direction first
-    const R Un = (D == 0) ? p.U : (D == 1) ? p.V : p.W;
-    R Fm1[5], Fm2[5], Wm2[5];
-    // heat_of expects momentum flux components in global order with U_n first; build
-    // the frame-aligned copies: (psi_0, u_n, u_t1, u_t2, psi_5) with t1, t2 = the other axes
-    constexpr int e1 = (D == 0) ? 2 : 1, e2 = (D == 2) ? 2 : 3;
-    constexpr int en = 1 + D;
-    Fm1[0] = m1[0];
-    Fm1[1] = m1[en];
-    Fm1[2] = m1[e1];
-    Fm1[3] = m1[e2];
-    Fm1[4] = m1[4];
-    Fm2[0] = m2[0];
-    Fm2[1] = m2[en];
-    Fm2[2] = m2[e1];
-    Fm2[3] = m2[e2];
-    Fm2[4] = m2[4];
-    R Wm1[5];
-    Wm1[0] = Wau[0];
-    Wm1[1] = Wau[en];
-    Wm1[2] = Wau[e1];
-    Wm1[3] = Wau[e2];
-    Wm1[4] = Wau[4];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) Wm2[k] = -Wm1[k];
-    const R Ut1 = (e1 == 1) ? p.U : (e1 == 2) ? p.V : p.W;
-    const R Ut2 = (e2 == 1) ? p.U : (e2 == 2) ? p.V : p.W;
-    const R H1 = heat_of(Fm1, Wm1, Un, Ut1, Ut2, 0);
-    const R H2 = heat_of(Fm2, Wm2, Un, Ut1, Ut2, 0);
-    F[4] += g.pr_fix * p.rho * (-tau * (H1 + H2));
-    Ft[4] += g.pr_fix * p.rho * H2;
+    // heat moments about U of the terms (a . u) g and A g: component 4 of
+    // <u_d psi'' phi> - U_d <psi'' phi>, with <psi'' (a . u) g> = Wau'' and <psi'' A g> = -Wau''
+    const R H1 = m1[4] - Ud * Wau[4];
+    const R H2 = m2[4] + Ud * Wau[4];
+    Fc[4] += g.pr_fix * p.rho * (-tau * (H1 + H2));
+    Ftc[4] += g.pr_fix * p.rho * H2;
   }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) F[k] = Ft[k] = R(0);
+  add_uncentred<true>(Fc, p.U, p.V, p.W, hs2, F);
+  add_uncentred<true>(Ftc, p.U, p.V, p.W, hs2, Ft);
 }
 
 template <class R>
@@ -458,26 +697,21 @@ DG_HD bool interior_flux(const R q[5], const R dq[3][5], const GasPar<R>& g, R F
   Prim<R> p;
   const bool ok = prim_of(q, g.gm1, p);
   const R ir = fdiv(R(1), p.rho);
-  R a[3][5];
+  const R h = fdiv(R(0.5), p.lam);
+  const R hs2 = R(0.5) * (p.U * p.U + p.V * p.V + p.W * p.W);
+  CTab<R> t;
+  cent_table(h, g.K, t);
+  CSolve<R> cs;
+  centred_solver(p.lam, h, g.K, cs);
+  R a[3][5], Wau[5], A[5];
+  centred_slopes(p, ir, hs2, cs, t, dq, a, Wau, A);
+  R aU[5];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    R b[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) b[k] = dq[i][k] * ir;
-    slope_solve(p, g.K, b, a[i]);
-  }
-  MomTab<R> t;
-  full_table(p, g.K, t);
-  R Wau[5] = {R(0), R(0), R(0), R(0), R(0)};
-  mom_adotu_psi<0, 0>(t, a, R(1), Wau);
-  R bA[5], A[5];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) bA[k] = -Wau[k];
-  slope_solve(p, g.K, bA, A);
+  for (int k = 0; k < 5; ++k) aU[k] = p.U * a[0][k] + p.V * a[1][k] + p.W * a[2][k];
   const R tau = fdiv(g.mu * R(2) * p.lam, p.rho) + g.tau_add;
-  interior_dir<0>(t, p, a, A, Wau, tau, g, F[0], Ft[0]);
-  interior_dir<1>(t, p, a, A, Wau, tau, g, F[1], Ft[1]);
-  interior_dir<2>(t, p, a, A, Wau, tau, g, F[2], Ft[2]);
+  interior_dir<0>(t, p, hs2, a, aU, A, Wau, tau, g, F[0], Ft[0]);
+  interior_dir<1>(t, p, hs2, a, aU, A, Wau, tau, g, F[1], Ft[1]);
+  interior_dir<2>(t, p, hs2, a, aU, A, Wau, tau, g, F[2], Ft[2]);
   return ok;
 }
 

@@ -25,7 +25,8 @@
 namespace opc {
 // Value numbering: every distinct (operation, operands) pair is counted once,
 // as a compiler's common-subexpression elimination would; operations with a
-// constant 0 or +-1 operand are free (folded).
+// compile-time constant 0 or +-1 operand are free (folded).  The point inputs
+// and gas parameters are run-time values with ids of their own.
 struct Tally {
   long add = 0, mul = 0, div = 0, sqrt = 0, exp = 0, erfc = 0;
   long flops() const { return add + mul + div; }
@@ -150,26 +151,30 @@ static int n_modes_dx(int k) {
   return c;
 }
 
+// A run-time input: a value with an id of its own, so that neither equal
+// values nor zeros or ones among the inputs fold operations away.
+static Cnt input(double x) { return Cnt(x, opc::next_id++); }
+
 static void state(Cnt q[5], Cnt dq[3][5], double s) {
-  const double rho = 1.1 + 0.1 * s, U = 0.3, V = -0.2, W = 0.1 * s, p = 71.4;
-  q[0] = rho;
-  q[1] = rho * U;
-  q[2] = rho * V;
-  q[3] = rho * W;
-  q[4] = p / 0.4 + 0.5 * rho * (U * U + V * V + W * W);
+  const double rho = 1.1 + 0.1 * s, U = 0.3, V = -0.2, W = 0.1 + 0.1 * s, p = 71.4;
+  q[0] = input(rho);
+  q[1] = input(rho * U);
+  q[2] = input(rho * V);
+  q[3] = input(rho * W);
+  q[4] = input(p / 0.4 + 0.5 * rho * (U * U + V * V + W * W));
   for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 5; ++k) dq[i][k] = 0.01 * (1 + i + k) * (k == 4 ? 100.0 : 1.0);
+    for (int k = 0; k < 5; ++k) dq[i][k] = input(0.01 * (1 + i + k) * (k == 4 ? 100.0 : 1.0));
 }
 
 static void emit(int order, int nq, double pr) {
   GasPar<Cnt> gp;
-  gp.K = 2.0;
-  gp.gm1 = 0.4;
-  gp.mu = 1.0 / 1600;
-  gp.tau_add = 0.0;
-  gp.pr_fix = 1.0 / pr - 1.0;
-  gp.dt = 3.3e-4;
-  gp.inv_dt = 1.0 / 3.3e-4;
+  gp.K = input(2.0);
+  gp.gm1 = input(0.4);
+  gp.mu = input(1.0 / 1600);
+  gp.tau_add = input(0.0);
+  gp.pr_fix = pr != 1.0 ? input(1.0 / pr - 1.0) : Cnt(0.0);  // the Pr = 1 kernels skip the heat terms
+  gp.dt = input(3.3e-4);
+  gp.inv_dt = input(1.0 / 3.3e-4);
   Cnt qL[5], dqL[3][5], qR[5], dqR[3][5], F[5], Ft[5], Fc[3][5], Ftc[3][5];
   state(qL, dqL, 0.0);
   state(qR, dqR, 1.0);

@@ -128,9 +128,23 @@ def test_uniform_flow_preserved(torch, api):
         rho, u, p = 1.3, (0.2, -0.4, 0.7), 2.0
         Q[0, 0], Q[1, 0], Q[2, 0], Q[3, 0] = rho, rho * u[0], rho * u[1], rho * u[2]
         Q[4, 0] = p / 0.4 + 0.5 * rho * sum(x * x for x in u)
-        L, Lt = s.residual(Q, 1e-2)
-        tol = 1e-12 if prec == 0 else 1e-4
-        assert float(L.abs().max()) < tol and float(Lt.abs().max()) < 10 * tol
+        dt = 1e-2
+        L, Lt = s.residual(Q, dt)
+        if prec == 0:
+            assert float(L.abs().max()) < 1e-12 and float(Lt.abs().max()) < 1e-11
+        else:
+            # FP32: the face and interior fluxes of the uniform state agree to rounding, so L is
+            # a few ulps of the largest flux component over the smallest cell width (times the
+            # basis factor 3 of the linear modes); F_t = 4 (I(dt) - 2 I(dt/2)) / dt^2 cancels
+            # the free-transport and equilibrium terms with the fit weight q = 4 x s^2 / dt
+            # (x = tau / dt, s = 1 - exp(-dt / (2 tau))), which multiplies that rounding
+            eps, fmax = 2.0 ** -24, 0.7 * (Q[4, 0, 0, 0, 0].item() + p)  # energy flux u_z (rho E + p)
+            h = 1 / 10
+            tau = 1e-3 / p
+            x, s_ = tau / dt, 1 - math.exp(-dt / (2 * tau))
+            q = 4 * x * s_ * s_ / dt
+            tol = 64 * eps * fmax * 3 / h
+            assert float(L.abs().max()) < tol and float(Lt.abs().max()) < q * tol
 
 
 def test_deterministic_and_graph_replay_bitwise(torch, api):
