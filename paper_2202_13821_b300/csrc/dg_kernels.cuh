@@ -158,9 +158,14 @@ constexpr int face_max_regs() {
   return cap > 255 ? 255 : cap;
 }
 
+// Per side and variable, a face stages the traces of its cell as two
+// polynomials in the tangential coordinates: the value at r_D = +-1 (NT
+// tangential modes) and the normal derivative there (degree ORDER - 1, NN
+// modes), each coefficient a signed sum of the cell's modes along D.
 template <class R, int ORDER, int NQ>
 struct FaceSmem {
-  static constexpr int NM = n_modes(ORDER), NT = n_tmodes(ORDER), NP = NQ * NQ, NC = 5 * NM;
+  static constexpr int NM = n_modes(ORDER), NT = n_tmodes(ORDER), NN = n_tmodes(ORDER - 1), NK = NT + NN;
+  static constexpr int NP = NQ * NQ, NC = 5 * NK;
   static constexpr size_t coef = sizeof(R) * NC * FB;  // one side
   static constexpr size_t fs = sizeof(R) * 10 * NP * FB;
   static constexpr size_t bytes = 2 * coef + fs;
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
     k_face(const Tin* __restrict__ Q, R* __restrict__ G, const GasPar<R> gp, const MeshDev m,
            unsigned* __restrict__ flag) {
   using S = FaceSmem<R, ORDER, NQ>;
-  constexpr int NM = S::NM, NT = S::NT, NP = S::NP, NC = S::NC;
+  constexpr int NM = S::NM, NT = S::NT, NN = S::NN, NK = S::NK, NP = S::NP;
   constexpr int T1 = tan1(D), T2 = tan2(D);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R(*cL)[FB] = reinterpret_cast<R(*)[FB]>(smem_raw);
@@ -192,11 +197,17 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   const int nx = m.nx, ny = m.ny, nz = m.nz;
   const long long nc = m.ncell;
 
-  // stage the coefficients of the left (-e_D) and right cells of each face
-  for (int e = tid; e < 2 * NC * FB; e += FB * NP) {
-    const int ff = e % FB, rest = e / FB, c = rest % NC, side = rest / NC;
+  // stage the face polynomials of the left (-e_D; traces at r_D = +1) and
+  // right (r_D = -1) cells of each face: P_n(+1) = 1, P_n(-1) = (-1)^n,
+  // P'_n(+1) = n(n+1)/2, P'_n(-1) = (-1)^(n+1) n(n+1)/2
+  for (int e = tid; e < 2 * 5 * FB; e += FB * NP) {
+    const int ff = e % FB, rest = e / FB, v = rest % 5, side = rest / 5;
     const int i = i0 + ff;
-    R val = R(0);
+    R Vt[NT], Nt[NN];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) Vt[t] = R(0);
+#pragma unroll
+    for (int t = 0; t < NN; ++t) Nt[t] = R(0);
     if (i < nx) {
       int ci = i, cj = j, ck = k;
       if (side == 0) {
@@ -204,12 +215,24 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
         if (D == 1) cj = wrapm(j - 1, ny);
         if (D == 2) ck = wrapm(k - 1, nz);
       }
-      val = (R)__ldg(Q + (size_t)c * nc + ((size_t)ck * ny + cj) * nx + ci);
+      const Tin* src = Q + (size_t)(v * NM) * nc + ((size_t)ck * ny + cj) * nx + ci;
+#pragma unroll
+      for (int mm = 0; mm < NM; ++mm) {
+        const R c = (R)__ldg(src + (size_t)mm * nc);
+        const int nD = mode_exp(mm, D), t = tmode_index(mode_exp(mm, T1), mode_exp(mm, T2));
+        const bool neg = side == 1 && (nD % 2 == 1);
+        Vt[t] += neg ? -c : c;
+        if (nD > 0) {
+          const R dc = R(nD * (nD + 1) / 2) * c;
+          Nt[t] += (side == 1 && nD % 2 == 0) ? -dc : dc;
+        }
+      }
     }
-    if (side == 0)
-      cL[c][ff] = val;
-    else
-      cR[c][ff] = val;
+    R(*dst)[FB] = side == 0 ? cL : cR;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) dst[v * NK + t][ff] = Vt[t];
+#pragma unroll
+    for (int t = 0; t < NN; ++t) dst[v * NK + NT + t][ff] = Nt[t];
   }
   __syncthreads();
 
@@ -217,13 +240,14 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   const bool active = i < nx;
   const int a = p / NQ, b = p % NQ;
   const R xa = gauss_xr<R>(NQ, a), xb = gauss_xr<R>(NQ, b);
-  R La[ORDER + 1], dLa[ORDER + 1], Lb[ORDER + 1], dLb[ORDER + 1];
+  // tangential basis at this point: phi_t, d phi_t / d r_1, d phi_t / d r_2
+  R Bt[NT], B1[NT], B2[NT];
 #pragma unroll
-  for (int n = 0; n <= ORDER; ++n) {
-    La[n] = leg<R>(n, xa);
-    dLa[n] = dleg<R>(n, xa);
-    Lb[n] = leg<R>(n, xb);
-    dLb[n] = dleg<R>(n, xb);
+  for (int t = 0; t < NT; ++t) {
+    const int tp = tmode_p(t), tq = tmode_q(t);
+    Bt[t] = leg<R>(tp, xa) * leg<R>(tq, xb);
+    B1[t] = tp > 0 ? dleg<R>(tp, xa) * leg<R>(tq, xb) : R(0);
+    B2[t] = tq > 0 ? leg<R>(tp, xa) * dleg<R>(tq, xb) : R(0);
   }
   // gradient scales: along D those of the left and right cells, tangential
   // ones shared by both cells (rectilinear mesh)
@@ -233,9 +257,9 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   const R sDs[2] = {cell_sc<R>(m, D, wrapm(cidx[D] - 1, nAx)), cell_sc<R>(m, D, cidx[D])};
   const R s1 = cell_sc<R>(m, T1, cidx[T1]), s2 = cell_sc<R>(m, T2, cidx[T2]);
 
-  // Each side in turn: traces at r_D = +1 of the left cell (side 0) or r_D = -1
-  // of the right cell (side 1), rotated to the local frame (axes D, D+1, D+2
-  // cyclic, momentum alike), folded into the side sums of Eq. (flux).
+  // Each side in turn: traces of the left cell (side 0) or the right cell
+  // (side 1) from its face polynomials, rotated to the local frame (axes D,
+  // D+1, D+2 cyclic, momentum alike), folded into the side sums of Eq. (flux).
   constexpr int A0 = D, A1 = (D + 1) % 3, A2 = (D + 2) % 3;
   const bool pr_fix = (gp.pr_fix != R(0));
   SideSums<R> sums;
@@ -243,22 +267,18 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   bool ok = true;
 #pragma unroll 1  // sides in turn, not interleaved: fewer live registers
   for (int side = 0; side < 2; ++side) {
+    const R(*cs)[FB] = side == 0 ? cL : cR;
     R q[5], dq[3][5];  // global axes
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       R s0 = R(0), gD = R(0), g1 = R(0), g2 = R(0);
 #pragma unroll
-      for (int mm = 0; mm < NM; ++mm) {
-        const int nD = mode_exp(mm, D), n1 = mode_exp(mm, T1), n2 = mode_exp(mm, T2);
-        // P_n(+1) = 1, P_n(-1) = (-1)^n; P'_n(+1) = n(n+1)/2, P'_n(-1) = (-1)^(n+1) n(n+1)/2
-        const R pn = (side == 0 || (nD % 2 == 0)) ? R(1) : R(-1);
-        const R dpn = R(nD * (nD + 1) / 2) * ((side == 0 || (nD % 2 == 1)) ? R(1) : R(-1));
-        const R c = (side == 0) ? cL[v * NM + mm][f] : cR[v * NM + mm][f];
-        const R t12 = La[n1] * Lb[n2];
-        s0 += c * (pn * t12);
-        gD += c * (dpn * t12);
-        g1 += c * (pn * dLa[n1] * Lb[n2]);
-        g2 += c * (pn * La[n1] * dLb[n2]);
+      for (int t = 0; t < NT; ++t) {
+        const R c = cs[v * NK + t][f];
+        s0 += c * Bt[t];
+        if (tmode_p(t) > 0) g1 += c * B1[t];
+        if (tmode_q(t) > 0) g2 += c * B2[t];
+        if (t < NN) gD += cs[v * NK + NT + t][f] * Bt[t];
       }
       q[v] = s0;
       dq[D][v] = gD * sDs[side];
@@ -507,9 +527,10 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
           const int e0 = mode_exp(mm, 0), e1 = mode_exp(mm, 1), e2 = mode_exp(mm, 2);
           const R cv = coef[v * NM + mm][cb];
           s0 += cv * (L1[0][e0] * L1[1][e1] * L1[2][e2]);
-          g0 += cv * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
-          g1 += cv * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
-          g2 += cv * (L1[0][e0] * L1[1][e1] * dL1[2][e2]);
+          // P'_0 = 0: modes constant along an axis have no gradient term there
+          if (e0 > 0) g0 += cv * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
+          if (e1 > 0) g1 += cv * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
+          if (e2 > 0) g2 += cv * (L1[0][e0] * L1[1][e1] * dL1[2][e2]);
         }
         q[v] = s0;
         dq[0][v] = g0 * sc[0];

@@ -192,23 +192,61 @@ static void emit(int order, int nq, double pr) {
     for (int k = 0; k < 5; ++k) outs.push_back(Ftc[d][k].id);
   const opc::Tally cell_ft = opc::live(outs);
 
-  const int NM = n_modes_(order), NT = n_tmodes_(order), NMx = n_modes_dx(order);
-  // traces, per side (face) or per point (cell): per mode the basis products
-  // (value 2, three gradients 2 each -> 8 multiplies; on a face the normal
-  // factor is a constant +-1 or n(n+1)/2, so 5), then 4 FMAs (8 flops) per
-  // variable, then 3 x 5 gradient scalings by 2/h.
-  const long trace_face_side = NM * 5 + NM * 5 * 8 + 15;
-  const long trace_cell = NM * 8 + NM * 5 * 8 + 15;
+  const int NM = n_modes_(order), NT = n_tmodes_(order), NMx = n_modes_dx(order), NN = n_tmodes_(order - 1);
+  const int np = nq * nq;
+  // Traces.  Basis factors P_0 = 1 and P'_1 = 1 are constants (folded);
+  // a product of f non-constant factors takes f - 1 multiplies, a term
+  // c * basis one FMA (2 flops), and the 3 x 5 gradients are scaled by 2/h.
+  auto muls = [](int f) { return f > 1 ? f - 1 : 0; };
+  // Face: per side and variable the value polynomial (NT tangential modes)
+  // and the normal-derivative polynomial (NN) are formed once per face from
+  // the cell's modes (a signed sum along the normal; factors n(n+1)/2 > 1
+  // multiply) and evaluated at each point with the tangential basis and its
+  // two derivatives (terms with P'_0 = 0 absent).
+  long face_basis = 0, face_terms = 0;
+  for (int a = 0; a <= order; ++a)
+    for (int b = 0; a + b <= order; ++b) {
+      face_basis += muls((a > 0) + (b > 0));
+      face_terms += 1 + (a > 0) + (b > 0) + (a + b <= order - 1);
+      if (a > 0) face_basis += muls((a > 1) + (b > 0));
+      if (b > 0) face_basis += muls((a > 0) + (b > 1));
+    }
+  long collapse = 0;  // per side and variable, per face
+  for (int m = 0, d = 0; d <= order; ++d)
+    for (int a = 0; a <= order - d; ++a)
+      for (int b = 0; a + b <= order - d; ++b, ++m) {
+        (void)m;
+        if (d > 0) collapse += 1;          // into the value polynomial (its first term is a move)
+        if (d > 0 && d != 1) collapse += 1;  // n(n+1)/2 multiply
+        if (d > 1) collapse += 1;            // into the normal polynomial
+      }
+  const long trace_face_side = 5 * face_terms * 2 + 15 + (5 * collapse + np - 1) / np;
+  // Cell: per point and mode the value product and, per axis with a non-zero
+  // exponent, the gradient product; one FMA per term.
+  long cell_basis = 0, cell_terms = 0;
+  for (int d = 0; d <= order; ++d)
+    for (int a = 0; a + d <= order; ++a)
+      for (int b = 0; a + b + d <= order; ++b) {
+        const int e[3] = {d, a, b};
+        cell_basis += muls((e[0] > 0) + (e[1] > 0) + (e[2] > 0));
+        cell_terms += 1;
+        for (int x = 0; x < 3; ++x)
+          if (e[x] > 0) {
+            cell_terms += 1;
+            cell_basis += muls((e[x] > 1) + (e[(x + 1) % 3] > 0) + (e[(x + 2) % 3] > 0));
+          }
+      }
+  const long trace_cell = cell_basis + 5 * cell_terms * 2 + 15;
   // face projection per point: 10 components x NT tangential modes FMA,
   // plus 10 weight multiplies
   const long proj_face = 10 * NT * 2 + 10;
   // cell projection per point: per direction only the NMx modes with a
   // non-zero derivative, 5 variables x (F, F_t) FMAs; plus 30 weight multiplies
   const long proj_cell = 3 * NMx * 5 * 2 * 2 + 30;
-  const long face_total = face.flops() + 2 * trace_face_side + proj_face;
+  const long face_total = face.flops() + face_basis + 2 * trace_face_side + proj_face;
   const long cell_total = cell.flops() + trace_cell + proj_cell;
   // F_t-only variants (stage 2 of S2O4): half of each projection
-  const long face_total_ft = face_ft.flops() + 2 * trace_face_side + 5 * NT * 2 + 5;
+  const long face_total_ft = face_ft.flops() + face_basis + 2 * trace_face_side + 5 * NT * 2 + 5;
   const long cell_total_ft = cell_ft.flops() + trace_cell + 3 * NMx * 5 * 2 + 15;
   printf(
       "{\"order\": %d, \"n_q\": %d, \"pr_fix\": %s, "
@@ -217,7 +255,7 @@ static void emit(int order, int nq, double pr) {
       "\"cell_point\": {\"flux_flops\": %ld, \"div\": %ld, \"sqrt\": %ld, \"exp\": %ld, \"erfc\": %ld, "
       "\"trace_flops\": %ld, \"proj_flops\": %ld, \"total_flops\": %ld, \"total_flops_ft\": %ld}}\n",
       order, nq, pr != 1.0 ? "true" : "false", face.flops(), face.div, face.sqrt, face.exp, face.erfc,
-      2 * trace_face_side, proj_face, face_total, face_total_ft, cell.flops(), cell.div, cell.sqrt, cell.exp,
+      face_basis + 2 * trace_face_side, proj_face, face_total, face_total_ft, cell.flops(), cell.div, cell.sqrt, cell.exp,
       cell.erfc, trace_cell, proj_cell, cell_total, cell_total_ft);
 }
 
