@@ -389,9 +389,12 @@ struct CellSmem {
   static constexpr size_t cvt = (LY::GW == 1 && std::is_same<Tin, R>::value) ? 0 : sizeof(R) * NC * CB;
   // cross-warp partial sums (only when a cell spans two warps)
   static constexpr size_t red = LY::GW == 1 ? 0 : sizeof(R) * CB * LY::GW * 2 * LY::NOP;
+  // GW = 1: the outputs of a tile (two kinds, NC x CB), double-buffered, so
+  // that they leave as rows of CB consecutive cells
+  static constexpr size_t out = LY::GW == 1 ? sizeof(R) * 2 * 2 * NC * CB : 0;
   static constexpr size_t tabs = sizeof(R) * NM + sizeof(int) * 6 * NM;
-  static constexpr size_t cvt_off = raw, red_off = raw + cvt, tab_off = raw + cvt + red;
-  static constexpr size_t bytes = raw + cvt + red + tabs;
+  static constexpr size_t cvt_off = raw, red_off = raw + cvt, out_off = raw + cvt + red, tab_off = out_off + out;
+  static constexpr size_t bytes = raw + cvt + red + out + tabs;
 };
 
 // Recursive-halving butterfly over the PG lanes of a group: in[N] per lane ->
@@ -495,9 +498,11 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     }
   }
 
+  const R h = (R)dt, h2 = (R)(dt * dt);
   // Everything after the staging of one tile (CB consecutive cells along x of
-  // row (j, k)), reading the coefficients from coef[NC][CB].
-  auto tile = [&](const int i0, const int j, const int k, const R (*coef)[CB]) {
+  // row (j, k)), reading the coefficients from coef[NC][CB].  With GW = 1 the
+  // results go to so[kind][NC][CB] in shared memory (written out by flush).
+  auto tile = [&](const int i0, const int j, const int k, const R (*coef)[CB], R (*so)[NC][CB]) {
     const size_t row = ((size_t)k * ny + j) * nx;
     // ---- interior flux of Eq. (flux-2) at this lane's Gauss point ----
     const bool active = (pidx < NP) && (i0 + cb < nx);
@@ -555,7 +560,6 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     // moments with the sign/parity of Eq. (operator), M^-1, and the stage
     // epilogue in the flux precision R; the accumulation into the stored FP64
     // state is the one FP64 operation.
-    const R h = (R)dt, h2 = (R)(dt * dt);
     auto finish = [&](int v, int n, int i, int cc, R sF, R sT) {
       const size_t cell = row + i;
       const size_t idx = (size_t)(v * NM + n) * nc + cell;
@@ -578,7 +582,18 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       if (mesh_nonuniform(m))  // 1/|K| = (2/h_x)(2/h_y)(2/h_z) / 8
         iM *= cell_sc<R>(m, 0, i) * cell_sc<R>(m, 1, j) * cell_sc<R>(m, 2, k) * R(0.125);
       const R Lv = sF * iM, Ltv = sT * iM;
-      if (MODE == MODE_RESIDUAL) {
+      if constexpr (GW == 1) {
+        const int o = v * NM + n;
+        if (MODE == MODE_RESIDUAL) {
+          so[0][o][cc] = Lv;
+          so[1][o][cc] = Ltv;
+        } else if (MODE == MODE_STAGE1) {
+          so[0][o][cc] = coef[o][cc] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
+          so[1][o][cc] = h * Lv + (h2 * R(1.0 / 6.0)) * Ltv;
+        } else {
+          so[0][o][cc] = Ltv;
+        }
+      } else if (MODE == MODE_RESIDUAL) {
         io.L[idx] = (double)Lv;
         io.Lt[idx] = (double)Ltv;
       } else if (MODE == MODE_STAGE1) {
@@ -675,12 +690,35 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       }
       cp_async_commit();
     };
-    long long t = blockIdx.x;
+    // outputs of tile tt (in so[bb]) -> global memory, a row of CB consecutive
+    // cells per (variable, mode): whole sectors instead of one value per row
+    R(*so)[2][NC][CB] = reinterpret_cast<R(*)[2][NC][CB]>(smem_raw + S::out_off);
+    auto flush = [&](long long tt, int bb) {
+      const int i0 = (int)(tt % ntx) * CB;
+      const size_t row = (size_t)(tt / ntx) * nx;
+      for (int e = tid; e < NC * CB; e += nthr) {
+        const int cc = e % CB, o = e / CB, i = i0 + cc;
+        if (i >= nx) continue;
+        const size_t idx = (size_t)o * nc + row + i;
+        if (MODE == MODE_RESIDUAL) {
+          io.L[idx] = (double)so[bb][0][o][cc];
+          io.Lt[idx] = (double)so[bb][1][o][cc];
+        } else if (MODE == MODE_STAGE1) {
+          io.Qs[idx] = so[bb][0][o][cc];
+          io.inc[idx] = so[bb][1][o][cc];
+        } else {
+          io.Qn[idx] = io.Qn[idx] + (double)(io.inc[idx] + (h2 * R(1.0 / 3.0)) * so[bb][0][o][cc]);
+        }
+      }
+    };
+    long long t = blockIdx.x, tprev = -1;
     if (t < ntiles) issue(t, 0);
-    for (int b = 0; t < ntiles; t += gridDim.x, b ^= 1) {
+    int b = 0;
+    for (; t < ntiles; t += gridDim.x, b ^= 1) {
       cp_async_wait_all();
       __syncthreads();  // tile t staged by all threads; every warp is done with buffer b ^ 1
       if (t + gridDim.x < ntiles) issue(t + gridDim.x, b ^ 1);
+      if (tprev >= 0) flush(tprev, b ^ 1);
       const R(*coef)[CB];
       if constexpr (std::is_same<Tin, R>::value) {
         coef = raw[b];
@@ -695,8 +733,11 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       }
       const int i0 = (int)(t % ntx) * CB;
       const long long r = t / ntx;
-      tile(i0, (int)(r % ny), (int)(r / ny), coef);
+      tile(i0, (int)(r % ny), (int)(r / ny), coef, so[b]);
+      tprev = t;
     }
+    __syncthreads();
+    if (tprev >= 0) flush(tprev, b ^ 1);
   } else {
     R(*coef)[CB] = reinterpret_cast<R(*)[CB]>(smem_raw + S::cvt_off);
     const int i0 = blockIdx.x * CB, j = blockIdx.y, k = blockIdx.z;
@@ -706,7 +747,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       coef[comp][cc] = (i < nx) ? (R)__ldg(Qin + (size_t)comp * nc + row + i) : R(0);
     }
     __syncthreads();
-    tile(i0, j, k, coef);
+    tile(i0, j, k, coef, nullptr);
   }
 }
 
