@@ -618,23 +618,59 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
 
     if constexpr (GW == 1) {
       // ---- volume projection fused with the epilogue: the PG lanes of a cell
-      // reduce PG outputs at a time by a butterfly, after which lane lg holds
-      // output c0 + lg of both kinds (F and F_t) and finishes it.  No
-      // cross-warp exchange, no second barrier. ----
-      constexpr int NO = 5 * NM, NOP1 = (NO + PG - 1) / PG * PG;
+      // reduce PG volume outputs (modes n >= 1, j = v (NM-1) + n-1) at a time
+      // by a butterfly, after which lane lg holds output j = blk PG + lg of
+      // both kinds (F and F_t) and finishes it.  When the last block of RM
+      // outputs fits twice into PG slots, its F and F_t sums share one
+      // butterfly (F in slots 0..RM-1, F_t in RM..2RM-1) and a shuffle pairs
+      // them.  The five mode-0 outputs have face terms only.  No cross-warp
+      // exchange, no second barrier. ----
+      constexpr int NV = 5 * (NM - 1), NB = NV / PG, RM = NV % PG;
+      constexpr bool PACK = MODE != MODE_STAGE2 && RM > 0 && 2 * RM <= PG;
+      constexpr int NBLK = NB + ((RM > 0 && !PACK) ? 1 : 0);
+      constexpr bool M0_LAST = RM > 0 && RM + 5 <= PG;  // mode 0 on the idle lanes of the last pass
+      const bool live = i0 + cb < nx;
+      auto vslot = [&](const R(&Fk)[3][5], int j) {
+        return j < NV ? vol_term(Fk, (j / (NM - 1)) * NM + 1 + j % (NM - 1)) : R(0);
+      };
+      // one finish per lane and pass: output j < NV of the pass, else (last
+      // pass) mode-0 output lg - RM
+      auto finish_pass = [&](int j, bool last, R sF, R sT) {
+        int v = j / (NM - 1), n = 1 + j % (NM - 1);
+        bool act = j < NV;
+        if (!act && last && M0_LAST && lg < RM + 5) {
+          v = lg - RM;
+          n = 0;
+          sF = sT = R(0);
+          act = true;
+        }
+        if (act && live) finish(v, n, i0 + cb, cb, sF, sT);
+      };
   #pragma unroll
-      for (int c0 = 0; c0 < NOP1; c0 += PG) {
+      for (int blk = 0; blk < NBLK; ++blk) {
         R vF[PG], vT[PG];
   #pragma unroll
         for (int oo = 0; oo < PG; ++oo) {
-          vF[oo] = vol_term(Fw, c0 + oo);
-          vT[oo] = vol_term(Ftw, c0 + oo);
+          vF[oo] = vslot(Fw, blk * PG + oo);
+          vT[oo] = vslot(Ftw, blk * PG + oo);
         }
         R oF[1], oT[1];
         group_reduce<PG, PG>(vF, oF, lg);
         group_reduce<PG, PG>(vT, oT, lg);
-        const int o = c0 + lg;
-        if (o < NO && i0 + cb < nx) finish(o / NM, o % NM, i0 + cb, cb, oF[0], oT[0]);
+        finish_pass(blk * PG + lg, !PACK && blk == NBLK - 1, oF[0], oT[0]);
+      }
+      if constexpr (PACK) {
+        R vv[PG];
+  #pragma unroll
+        for (int oo = 0; oo < PG; ++oo)
+          vv[oo] = oo < RM ? vslot(Fw, NB * PG + oo) : (oo < 2 * RM ? vslot(Ftw, NB * PG + oo - RM) : R(0));
+        R o1[1];
+        group_reduce<PG, PG>(vv, o1, lg);
+        const R oT = __shfl_down_sync(0xffffffffu, o1[0], RM);  // lane lg < RM: F_t sum from lane lg + RM
+        finish_pass(lg < RM ? NB * PG + lg : NV, true, o1[0], oT);
+      }
+      if constexpr (!M0_LAST) {
+        if (lg >= PG - 5 && live) finish(lg - (PG - 5), 0, i0 + cb, cb, R(0), R(0));
       }
     } else {
       // ---- a cell spans GW warps: per-warp butterflies over the modes n >= 1,
