@@ -90,8 +90,9 @@ typedef struct {
  * paper; Pr != 1 adds (1/Pr - 1) times the heat flux of the same distribution
  * to the energy flux, which the paper does not define).  opts may be NULL
  * (n_q = order+1, FP64, tau_eps = 0).  Uses the current CUDA device.
- * Allocates the scratch: 2 stage buffers of the state size plus the face
- * moments (3 * 10 * (k+1)(k+2)/2 values per cell in the flux precision). */
+ * Allocates the scratch: 2 stage buffers with the state's values in the flux
+ * precision (3 on an FP32-mixed context: also the FP32 state copy) plus the
+ * face moments (3 * 10 * (k+1)(k+2)/2 values per cell in the flux precision). */
 int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, double Pr, const dghgks_opts* opts,
                 dghgks_ctx** out);
 
@@ -119,18 +120,24 @@ int dghgks_residual(dghgks_ctx* ctx, const double* Q, double dt, double* L, doub
  * Asynchronous; consecutive calls on one context must share a stream. */
 int dghgks_step(dghgks_ctx* ctx, double* Q, double dt, void* stream);
 
-/* nsteps S2O4 steps in place on the device state Q, replaying a CUDA graph
- * of one step (8 kernel launches) on `stream`.  The graph is captured on a
+/* nsteps S2O4 steps in place on the device state Q, replaying CUDA graphs
+ * of one step (8 kernel launches) on `stream`.  The graphs are captured on a
  * private stream at the first call and re-captured when Q, dt or the
  * viscosity (dghgks_set_mu) changes (the executable graph is updated in
- * place when possible).  Results are
- * identical to nsteps calls of dghgks_step.  Asynchronous.  Must not be
- * called while `stream` itself is being captured; profiling records nothing
- * for graph replays. */
+ * place when possible).  On an FP32-mixed context the first step reads the
+ * FP64 state and every step's state update also writes the state rounded to
+ * FP32 into a library buffer, which the stage-1 kernels of the following
+ * steps read instead of rounding Q themselves (the same values; a second
+ * graph); Q may therefore change between calls but not during one.  Results
+ * are identical to nsteps calls of dghgks_step.  Asynchronous.  Must not be
+ * called while `stream` itself is being captured.  With profiling on
+ * (dghgks_profile) the same launches are enqueued directly, each recorded,
+ * instead of replaying the graphs. */
 int dghgks_steps(dghgks_ctx* ctx, double* Q, double dt, int nsteps, void* stream);
 
 /* nsteps S2O4 steps on a HOST state (pinned or pageable): copies Q_host to
- * the device, steps, and copies the result back; if ek_host is not NULL it
+ * the device, steps (with the FP32 state copy between steps, as
+ * dghgks_steps), and copies the result back; if ek_host is not NULL it
  * receives E_k (as dghgks_kinetic_energy with rho0) after every step (host
  * memory, nsteps doubles).  The E_k of step n runs on a second, library-owned
  * stream beside step n+1, whose state update waits for it; results are

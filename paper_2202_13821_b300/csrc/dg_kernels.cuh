@@ -446,7 +446,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 //   MODE 0: L, Lt (FP64, caller's)
 //   MODE 1: Qs = Q* and inc = dt L + dt^2/6 L_t, both in the flux precision R
 //           (the stage-2 kernels read Q* in R; nothing is lost)
-//   MODE 2: Qn (FP64 state, updated in place) += inc + dt^2/3 L_t(Q*)
+//   MODE 2: Qn (FP64 state, updated in place) += inc + dt^2/3 L_t(Q*); when Qf
+//           is not null, also Qf = the updated state rounded to R (the next
+//           step's stage-1 kernels read it instead of converting Qn)
 template <class R>
 struct StageIO {
   double* L;
@@ -454,6 +456,7 @@ struct StageIO {
   R* Qs;
   R* inc;
   double* Qn;
+  R* Qf;
 };
 
 // Resident CTAs of k_cell per SM requested from the compiler (FP32): 2 gives
@@ -600,7 +603,9 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         io.Qs[idx] = coef[v * NM + n][cc] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
         io.inc[idx] = h * Lv + (h2 * R(1.0 / 6.0)) * Ltv;
       } else {
-        io.Qn[idx] = io.Qn[idx] + (double)(io.inc[idx] + (h2 * R(1.0 / 3.0)) * Ltv);
+        const double q = io.Qn[idx] + (double)(io.inc[idx] + (h2 * R(1.0 / 3.0)) * Ltv);
+        io.Qn[idx] = q;
+        if (io.Qf) io.Qf[idx] = (R)q;
       }
     };
     // this lane's contribution to output o (v = o / NM, mode n = o % NM; mode 0 has no volume term)
@@ -743,7 +748,9 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
           io.Qs[idx] = so[bb][0][o][cc];
           io.inc[idx] = so[bb][1][o][cc];
         } else {
-          io.Qn[idx] = io.Qn[idx] + (double)(io.inc[idx] + (h2 * R(1.0 / 3.0)) * so[bb][0][o][cc]);
+          const double q = io.Qn[idx] + (double)(io.inc[idx] + (h2 * R(1.0 / 3.0)) * so[bb][0][o][cc]);
+          io.Qn[idx] = q;
+          if (io.Qf) io.Qf[idx] = (R)q;
         }
       }
     };

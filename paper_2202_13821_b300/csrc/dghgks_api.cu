@@ -37,6 +37,8 @@ struct dghgks_ctx {
   int order = 0, nq = 0, nm = 0, nt = 0, precision = 0;
   double gamma = 1.4, K = 2.0, mu = 0, Pr = 1, tau_eps = 0;
   void* Qs = nullptr;   // Q* (stage-1 output), flux precision
+  void* Qf = nullptr;   // FP32-mixed: the state rounded to FP32 by a stage-2 pass, read by the
+                        // next step's stage-1 kernels within one dghgks_steps / dghgks_run_host call
   void* Inc = nullptr;  // dt L + dt^2/6 L_t (stage-1 output), flux precision
   void* G = nullptr;      // face moments [3][cells][10][NT] (face-major), flux precision
   unsigned* flag = nullptr;
@@ -58,12 +60,13 @@ struct dghgks_ctx {
   int prof_n = 0;
   cudaEvent_t* prof_ev = nullptr;  // [2 * kProfMax]
   int* prof_kind = nullptr;        // [kProfMax]
-  // captured step graph
+  // captured step graphs: [0] a step on the FP64 state, [1] a step on the FP32 copy
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  double* g_Q = nullptr;  // arguments the captured graph was built with
-  double g_dt = 0.0;
-  double g_mu = -1.0;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  double* g_Q[2] = {nullptr, nullptr};  // arguments each captured graph was built with
+  double g_dt[2] = {0.0, 0.0};
+  double g_mu[2] = {-1.0, -1.0};
+  bool g_out[2] = {false, false};
   char err[512] = {0};
 };
 
@@ -140,13 +143,16 @@ struct ProfScope {
   }
 };
 
+enum { FACES_FP64 = 0, FACES_COPY = 1, FACES_QSTAR = 2 };
+
 struct Ops {
   cudaError_t (*set_attrs)();
-  // face pass on a state stored in FP64 (q_in_r = false), or the stage-2 pass on
-  // Q* stored in the flux precision (q_in_r = true; F_t moments only)
-  void (*faces)(dghgks_ctx*, const void*, bool, double, cudaStream_t);
-  // cell pass: MODE_RESIDUAL (Q, L, Lt), MODE_STAGE1 (Q^n), MODE_STAGE2 (Q^n updated in place)
-  void (*cell)(dghgks_ctx*, int, double*, double*, double*, double, cudaStream_t);
+  // face pass: FACES_FP64 on the FP64 state, FACES_COPY on its FP32 copy Qf,
+  // FACES_QSTAR the stage-2 pass on Q* (F_t moments only)
+  void (*faces)(dghgks_ctx*, const void*, int, double, cudaStream_t);
+  // cell pass: MODE_RESIDUAL (Q, L, Lt), MODE_STAGE1 (Q^n, or its copy Qf when
+  // copy_in), MODE_STAGE2 (Q^n updated in place; Qf written when copy_out)
+  void (*cell)(dghgks_ctx*, int, double*, double*, double*, double, cudaStream_t, bool copy_in, bool copy_out);
   void (*ek)(dghgks_ctx*, const double*, cudaStream_t);
   void (*enstrophy)(dghgks_ctx*, const double*, cudaStream_t);
   size_t r_size;
@@ -163,11 +169,15 @@ struct Impl {
     DG_ATTR((k_face<R, ORDER, NQ, 0, double>), FS::bytes)
     DG_ATTR((k_face<R, ORDER, NQ, 1, double>), FS::bytes)
     DG_ATTR((k_face<R, ORDER, NQ, 2, double>), FS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 0, R, false>), FS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 1, R, false>), FS::bytes)
+    DG_ATTR((k_face<R, ORDER, NQ, 2, R, false>), FS::bytes)
     DG_ATTR((k_face<R, ORDER, NQ, 0, R, true>), FS::bytes)
     DG_ATTR((k_face<R, ORDER, NQ, 1, R, true>), FS::bytes)
     DG_ATTR((k_face<R, ORDER, NQ, 2, R, true>), FS::bytes)
     DG_ATTR((k_cell<R, ORDER, NQ, MODE_RESIDUAL, double>), (CellSmem<R, ORDER, NQ, double>::bytes))
     DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, double>), (CellSmem<R, ORDER, NQ, double>::bytes))
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, R>), (CellSmem<R, ORDER, NQ, R>::bytes))
     DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE2, R>), (CellSmem<R, ORDER, NQ, R>::bytes))
 #undef DG_ATTR
     return e;
@@ -195,9 +205,11 @@ struct Impl {
     c->launches += 3;
   }
 
-  static void faces(dghgks_ctx* c, const void* Q, bool q_in_r, double dt, cudaStream_t s) {
-    if (q_in_r)  // the stage-2 pass on Q*: F_t moments only
+  static void faces(dghgks_ctx* c, const void* Q, int kind, double dt, cudaStream_t s) {
+    if (kind == FACES_QSTAR)  // the stage-2 pass on Q*: F_t moments only
       faces_t<R, true>(c, static_cast<const R*>(Q), dt, s);
+    else if (kind == FACES_COPY)
+      faces_t<R, false>(c, static_cast<const R*>(Q), dt, s);
     else
       faces_t<double, false>(c, static_cast<const double*>(Q), dt, s);
   }
@@ -211,7 +223,8 @@ struct Impl {
     k_cell<R, ORDER, NQ, MODE, Tin><<<grid, CellLayout<ORDER, NQ>::WARPS * 32, smem, s>>>(Qin, G, io, g, m, dt, c->flag);
   }
 
-  static void cell(dghgks_ctx* c, int mode, double* Q, double* L, double* Lt, double dt, cudaStream_t s) {
+  static void cell(dghgks_ctx* c, int mode, double* Q, double* L, double* Lt, double dt, cudaStream_t s,
+                   bool copy_in, bool copy_out) {
     const GasPar<R> g = gas_par<R>(c, dt);
     const MeshDev m = mesh_dev(c);
     const R* G = static_cast<const R*>(c->G);
@@ -221,9 +234,12 @@ struct Impl {
     io.Qs = static_cast<R*>(c->Qs);
     io.inc = static_cast<R*>(c->Inc);
     io.Qn = Q;
+    io.Qf = copy_out ? static_cast<R*>(c->Qf) : nullptr;
     ProfScope ps(c, 3 + mode, s);
     if (mode == MODE_RESIDUAL)
       cell_t<MODE_RESIDUAL, double>(c, Q, G, io, g, m, dt, s);
+    else if (mode == MODE_STAGE1 && copy_in)
+      cell_t<MODE_STAGE1, R>(c, static_cast<const R*>(c->Qf), G, io, g, m, dt, s);
     else if (mode == MODE_STAGE1)
       cell_t<MODE_STAGE1, double>(c, Q, G, io, g, m, dt, s);
     else
@@ -317,7 +333,8 @@ int read_flag(dghgks_ctx* c, cudaStream_t s) {
 
 extern "C" {
 
-static void enqueue_step(dghgks_ctx* c, double* Q, double dt, cudaStream_t s, cudaEvent_t before_write);
+static void enqueue_step(dghgks_ctx* c, double* Q, double dt, cudaStream_t s, cudaEvent_t before_write,
+                         bool copy_in = false, bool copy_out = false);
 
 int dghgks_gauss_rule(int n, double* x, double* w) {
   if (n < 1 || n > 5 || !x || !w) return DGHGKS_EARG;
@@ -409,6 +426,7 @@ int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, dou
   if (!rc) rc = cuda_check(c, ops->set_attrs(), "cudaFuncSetAttribute");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->Qs, stage), "cudaMalloc(Q*)");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->Inc, stage), "cudaMalloc(stage increment)");
+  if (!rc && precision != DGHGKS_FP64) rc = cuda_check(c, cudaMalloc(&c->Qf, stage), "cudaMalloc(FP32 state copy)");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->G, gbytes), "cudaMalloc(face moments)");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->flag, sizeof(unsigned)), "cudaMalloc(flag)");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->part, sizeof(double) * 5 * kRedBlocks), "cudaMalloc(partials)");
@@ -436,7 +454,8 @@ int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, dou
 
 void dghgks_destroy(dghgks_ctx* c) {
   if (!c) return;
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (int k = 0; k < 2; ++k)
+    if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->prof_ev) {
     for (int e = 0; e < 2 * kProfMax; ++e) cudaEventDestroy(c->prof_ev[e]);
@@ -444,6 +463,7 @@ void dghgks_destroy(dghgks_ctx* c) {
     delete[] c->prof_kind;
   }
   cudaFree(c->Qs);
+  cudaFree(c->Qf);
   cudaFree(c->Inc);
   cudaFree(c->G);
   cudaFree(c->flag);
@@ -481,8 +501,8 @@ int dghgks_residual(dghgks_ctx* c, const double* Q, double dt, double* L, double
   if (!(dt > 0)) return fail(c, DGHGKS_EARG, "dt must be > 0");
   if (L == Q || Lt == Q || L == Lt) return fail(c, DGHGKS_EARG, "L, Lt and Q must be distinct buffers");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  c->ops->faces(c, Q, false, dt, s);
-  c->ops->cell(c, MODE_RESIDUAL, const_cast<double*>(Q), L, Lt, dt, s);
+  c->ops->faces(c, Q, FACES_FP64, dt, s);
+  c->ops->cell(c, MODE_RESIDUAL, const_cast<double*>(Q), L, Lt, dt, s, false, false);
   return after_launch(c, "residual launch");
 }
 
@@ -497,13 +517,56 @@ int dghgks_step(dghgks_ctx* c, double* Q, double dt, void* stream) {
 
 // Enqueue the 8 launches of one S2O4 step on s.  before_write (may be null): an event that the stage-2
 // cell kernel, the only writer of Q, waits for (readers of Q^n on another
-// stream).
-static void enqueue_step(dghgks_ctx* c, double* Q, double dt, cudaStream_t s, cudaEvent_t before_write) {
-  c->ops->faces(c, Q, false, dt, s);
-  c->ops->cell(c, MODE_STAGE1, Q, nullptr, nullptr, dt, s);  // Q*, inc
-  c->ops->faces(c, c->Qs, true, dt, s);
+// stream).  FP32-mixed contexts: copy_in = the stage-1 kernels read the FP32
+// copy Qf of Q^n that the previous step wrote (the values they would convert
+// Q^n to); copy_out = the stage-2 cell kernel writes Qf for the next step.
+static void enqueue_step(dghgks_ctx* c, double* Q, double dt, cudaStream_t s, cudaEvent_t before_write,
+                         bool copy_in, bool copy_out) {
+  copy_in = copy_in && c->Qf;
+  copy_out = copy_out && c->Qf;
+  c->ops->faces(c, copy_in ? c->Qf : Q, copy_in ? FACES_COPY : FACES_FP64, dt, s);
+  c->ops->cell(c, MODE_STAGE1, Q, nullptr, nullptr, dt, s, copy_in, false);  // Q*, inc
+  c->ops->faces(c, c->Qs, FACES_QSTAR, dt, s);
   if (before_write) cudaStreamWaitEvent(s, before_write, 0);
-  c->ops->cell(c, MODE_STAGE2, Q, nullptr, nullptr, dt, s);  // Q += inc + dt^2/3 L_t(Q*)
+  c->ops->cell(c, MODE_STAGE2, Q, nullptr, nullptr, dt, s, false, copy_out);  // Q += inc + dt^2/3 L_t(Q*)
+}
+
+// Capture (or update) step graph k: one step on Q with the FP64 state (k = 0)
+// or its FP32 copy (k = 1) as the stage-1 input, writing the copy when copy_out.
+// The kernels' arguments (state pointer, dt and the gas parameters derived from
+// dt and mu) are baked into the graph: capture again when one changed.
+static int ensure_graph(dghgks_ctx* c, int k, double* Q, double dt, bool copy_out) {
+  if (c->gexec[k] && c->g_Q[k] == Q && c->g_dt[k] == dt && c->g_mu[k] == c->mu && c->g_out[k] == copy_out)
+    return DGHGKS_OK;
+  const bool prof = c->prof;
+  const int64_t launches = c->launches;
+  c->prof = false;
+  cudaGraph_t graph = nullptr;
+  if (int rc = cuda_check(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "capture"))
+    return rc;
+  enqueue_step(c, Q, dt, c->cap_stream, nullptr, k == 1, copy_out);
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+  c->prof = prof;
+  c->launches = launches;
+  if (int rc = cuda_check(c, e, "end capture")) return rc;
+  bool updated = false;
+  if (c->gexec[k]) {
+    cudaGraphExecUpdateResultInfo info;
+    updated = cudaGraphExecUpdate(c->gexec[k], graph, &info) == cudaSuccess;
+    if (!updated) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(c->gexec[k]);
+      c->gexec[k] = nullptr;
+    }
+  }
+  if (!updated) e = cudaGraphInstantiate(&c->gexec[k], graph, 0);
+  cudaGraphDestroy(graph);
+  if (int rc = cuda_check(c, e, "graph instantiate")) return rc;
+  c->g_Q[k] = Q;
+  c->g_dt[k] = dt;
+  c->g_mu[k] = c->mu;
+  c->g_out[k] = copy_out;
+  return DGHGKS_OK;
 }
 
 int dghgks_steps(dghgks_ctx* c, double* Q, double dt, int nsteps, void* stream) {
@@ -514,39 +577,19 @@ int dghgks_steps(dghgks_ctx* c, double* Q, double dt, int nsteps, void* stream) 
   if (!c->cap_stream)
     if (int rc = cuda_check(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream"))
       return rc;
-  // the kernels' arguments (state pointer, dt and the gas parameters derived
-  // from dt and mu) are baked into the graph: capture again when one changed
-  if (!c->gexec || c->g_Q != Q || c->g_dt != dt || c->g_mu != c->mu) {
-    const bool prof = c->prof;
-    const int64_t launches = c->launches;
-    c->prof = false;
-    cudaGraph_t graph = nullptr;
-    if (int rc = cuda_check(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "capture"))
-      return rc;
-    enqueue_step(c, Q, dt, c->cap_stream, nullptr);
-    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
-    c->prof = prof;
-    c->launches = launches;
-    if (int rc = cuda_check(c, e, "end capture")) return rc;
-    bool updated = false;
-    if (c->gexec) {
-      cudaGraphExecUpdateResultInfo info;
-      updated = cudaGraphExecUpdate(c->gexec, graph, &info) == cudaSuccess;
-      if (!updated) {
-        cudaGetLastError();
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-      }
-    }
-    if (!updated) e = cudaGraphInstantiate(&c->gexec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (int rc = cuda_check(c, e, "graph instantiate")) return rc;
-    c->g_Q = Q;
-    c->g_dt = dt;
-    c->g_mu = c->mu;
+  // the first step reads the FP64 state; on FP32-mixed contexts it and every
+  // later one write the state's FP32 copy, which the later steps read
+  const bool copy = c->Qf && nsteps > 1;
+  if (c->prof) {  // profiling: the same launches enqueued directly, each recorded
+    for (int n = 0; n < nsteps; ++n) enqueue_step(c, Q, dt, s, nullptr, copy && n > 0, copy);
+    return after_launch(c, "step launch");
   }
+  if (nsteps > 0)
+    if (int rc = ensure_graph(c, 0, Q, dt, copy)) return rc;
+  if (copy)
+    if (int rc = ensure_graph(c, 1, Q, dt, true)) return rc;
   for (int n = 0; n < nsteps; ++n)
-    if (int rc = cuda_check(c, cudaGraphLaunch(c->gexec, s), "graph launch")) return rc;
+    if (int rc = cuda_check(c, cudaGraphLaunch(c->gexec[copy && n > 0 ? 1 : 0], s), "graph launch")) return rc;
   c->launches += 8 * (int64_t)nsteps;
   return DGHGKS_OK;
 }
@@ -652,7 +695,7 @@ int dghgks_run_host(dghgks_ctx* c, double* Q_host, double dt, int nsteps, double
   }
   bool ek_pending = false;
   for (int n = 0; n < nsteps; ++n) {
-    enqueue_step(c, c->Qdev, dt, s, ek_pending ? c->ev_ek : nullptr);
+    enqueue_step(c, c->Qdev, dt, s, ek_pending ? c->ev_ek : nullptr, n > 0, n + 1 < nsteps);
     if (int rc = after_launch(c, "step launch")) return rc;
     if (ek_host) {
       cudaStream_t e = c->ek_stream;
@@ -768,8 +811,8 @@ int dghgks_adjoint_step(dghgks_ctx* c, const double* Qn, const double* lam_next,
   if (int rc = adj_prepare(c)) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // recompute Q* from the checkpoint (one forward stage)
-  c->ops->faces(c, Qn, false, dt, s);
-  c->ops->cell(c, MODE_STAGE1, const_cast<double*>(Qn), nullptr, nullptr, dt, s);
+  c->ops->faces(c, Qn, FACES_FP64, dt, s);
+  c->ops->cell(c, MODE_STAGE1, const_cast<double*>(Qn), nullptr, nullptr, dt, s, false, false);
   const double* Qs = static_cast<const double*>(c->Qs);
   // stage 2 at Q*: only L_t(Q*) enters Q^{n+1}, with dt^2/3
   AdjIO io2{};

@@ -96,6 +96,7 @@ void launch(const MeshDev& m, const GasPar<R>& g, const double* Q, double* L, do
   io.Qs = nullptr;
   io.inc = nullptr;
   io.Qn = nullptr;
+  io.Qf = nullptr;
   dim3 cgrid;
   size_t csmem = 0;
   cell_launch_config<R, ORDER, NQ, MODE_RESIDUAL, double>(m, cgrid, csmem);

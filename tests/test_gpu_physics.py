@@ -167,6 +167,32 @@ def test_deterministic_and_graph_replay_bitwise(torch, api):
         assert torch.equal(D, E)
 
 
+def test_fp32_state_copy_stays_within_one_call(torch, api):
+    """FP32-mixed dghgks_steps: the steps after the first read the FP32 copy of the state that the
+    step before wrote; the first step of every call reads the FP64 state, so a state changed between
+    calls is what the next call steps, and a profiled call (launches enqueued directly, each
+    recorded) gives the graph replay's result."""
+    from paper_2202_13821_b300 import inputs
+
+    s = api.Solver((20, 12, 9), **TGV, order=2, mu=1 / 1600, Pr=0.72, precision=1)
+    Q0 = inputs.tgv_state((20, 12, 9), 2, perturb=1e-3, device="cuda")
+    Q1 = Q0.clone()
+    Q1[0, 0] *= 1.01  # another state: density raised by 1 %
+    A = Q0.clone()
+    s.steps(A, 4e-3, 3)  # leaves the FP32 copy of A behind
+    B, C, D = Q1.clone(), Q1.clone(), Q1.clone()
+    s.steps(B, 4e-3, 2)
+    s.step(C, 4e-3, 2)
+    s.profile(True)
+    s.steps(D, 4e-3, 2)
+    prof = s.profile_read()
+    s.profile(False)
+    s.status()
+    assert torch.equal(B, C) and torch.equal(B, D)
+    assert sum(n for _, n in prof.values()) == 16  # 8 launches per step, all recorded
+    assert not torch.equal(A, B)
+
+
 def test_run_host_matches_device_steps(torch, api):
     """dghgks_run_host (host state in and out, E_k of each step on a second stream beside the next
     step) gives bitwise the state and E_k history of device steps with E_k after each."""
