@@ -301,18 +301,22 @@ def algorithmic_bytes(kernel, precision):
     """HBM bytes per cell of one launch, mean of the two stages of a step (P2: 50 state coefficients,
     60 face moments per face): each value read or written once, neighbours' data counted once.
 
-    k_face stage 1 reads the FP64 state and writes the F and F_t moments; stage 2 reads Q* (flux
-    precision) and writes the F_t moments.  k_cell stage 1 reads the FP64 state and the moments of
-    its faces and writes Q* and inc; stage 2 reads Q*, inc, the F_t moments and the FP64 state and
-    writes the state."""
+    k_face stage 1 reads the state and writes the F and F_t moments; stage 2 reads Q* (flux
+    precision) and writes the F_t moments.  k_cell stage 1 reads the state and the moments of its
+    faces and writes Q* and inc; stage 2 reads Q*, inc, the F_t moments and the FP64 state and
+    writes the state.  FP32-mixed steps after the first of a dghgks_steps call (the steady state of
+    the timed region) read the state's FP32 copy at stage 1, which stage 2 writes besides the FP64
+    state."""
     r = 4 if precision == 1 else 8
     coef, mom = 5 * 10, 10 * 6
+    state_in = coef * r  # FP32 copy (FP32-mixed) or the FP64 state
+    copy_out = coef * 4 if precision == 1 else 0
     if kernel == "k_face":
-        s1 = coef * 8 + mom * r
+        s1 = state_in + mom * r
         s2 = coef * r + mom // 2 * r
     else:
-        s1 = coef * 8 + 3 * mom * r + 2 * coef * r  # six faces, each shared by two cells
-        s2 = 2 * coef * r + 3 * (mom // 2) * r + 2 * coef * 8
+        s1 = state_in + 3 * mom * r + 2 * coef * r  # six faces, each shared by two cells
+        s2 = 2 * coef * r + 3 * (mom // 2) * r + 2 * coef * 8 + copy_out
     return (s1 + s2) / 2
 
 
