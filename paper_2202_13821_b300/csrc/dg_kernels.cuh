@@ -162,15 +162,38 @@ constexpr int face_max_regs() {
 // polynomials in the tangential coordinates: the value at r_D = +-1 (NT
 // tangential modes) and the normal derivative there (degree ORDER - 1, NN
 // modes), each coefficient a signed sum of the cell's modes along D.
+// A face's polynomials are contiguous in its row, each variable's NK values
+// padded to whole 16-byte groups (VP values), the row pitch an odd number of
+// 16-byte groups, so that the points read them with conflict-free 16-byte loads.
 template <class R, int ORDER, int NQ>
 struct FaceSmem {
   static constexpr int NM = n_modes(ORDER), NT = n_tmodes(ORDER), NN = n_tmodes(ORDER - 1), NK = NT + NN;
-  static constexpr int NP = NQ * NQ, NC = 5 * NK;
-  static constexpr size_t coef = sizeof(R) * NC * FB;  // one side
+  static constexpr int NP = NQ * NQ, W16 = 16 / sizeof(R);
+  static constexpr int VP = (NK + W16 - 1) / W16 * W16;
+  static constexpr int PITCH = ((5 * VP / W16) % 2 == 1) ? 5 * VP : 5 * VP + W16;
+  static constexpr size_t coef = sizeof(R) * PITCH * FB;  // one side
   static constexpr size_t fs = sizeof(R) * 10 * NP * FB;
   static constexpr size_t bytes = 2 * coef + fs;
   static_assert(sizeof(R) * FB * 10 * NT <= 2 * coef, "face moments must fit the staging area");
 };
+
+// N consecutive values (N a multiple of 16 / sizeof(R), 16-byte aligned) from shared memory
+template <int N, class R>
+__device__ __forceinline__ void lds16(const R* p, R (&c)[N]) {
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+      const float4 q = reinterpret_cast<const float4*>(p)[i];
+      c[4 * i] = q.x, c[4 * i + 1] = q.y, c[4 * i + 2] = q.z, c[4 * i + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const double2 q = reinterpret_cast<const double2*>(p)[i];
+      c[2 * i] = q.x, c[2 * i + 1] = q.y;
+    }
+  }
+}
 
 __device__ __forceinline__ int wrapm(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
@@ -184,11 +207,11 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
     k_face(const Tin* __restrict__ Q, R* __restrict__ G, const GasPar<R> gp, const MeshDev m,
            unsigned* __restrict__ flag) {
   using S = FaceSmem<R, ORDER, NQ>;
-  constexpr int NM = S::NM, NT = S::NT, NN = S::NN, NK = S::NK, NP = S::NP;
+  constexpr int NM = S::NM, NT = S::NT, NN = S::NN, NP = S::NP, VP = S::VP, PITCH = S::PITCH;
   constexpr int T1 = tan1(D), T2 = tan2(D);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R(*cL)[FB] = reinterpret_cast<R(*)[FB]>(smem_raw);
-  R(*cR)[FB] = reinterpret_cast<R(*)[FB]>(smem_raw + S::coef);
+  R(*cL)[PITCH] = reinterpret_cast<R(*)[PITCH]>(smem_raw);  // [face][var VP + poly value]
+  R(*cR)[PITCH] = reinterpret_cast<R(*)[PITCH]>(smem_raw + S::coef);
   R(*Fs)[NP][FB] = reinterpret_cast<R(*)[NP][FB]>(smem_raw + 2 * S::coef);
 
   const int tid = threadIdx.x;
@@ -228,11 +251,11 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
         }
       }
     }
-    R(*dst)[FB] = side == 0 ? cL : cR;
+    R* dst = (side == 0 ? cL : cR)[ff] + v * VP;
 #pragma unroll
-    for (int t = 0; t < NT; ++t) dst[v * NK + t][ff] = Vt[t];
+    for (int t = 0; t < NT; ++t) dst[t] = Vt[t];
 #pragma unroll
-    for (int t = 0; t < NN; ++t) dst[v * NK + NT + t][ff] = Nt[t];
+    for (int t = 0; t < NN; ++t) dst[NT + t] = Nt[t];
   }
   __syncthreads();
 
@@ -267,18 +290,20 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   bool ok = true;
 #pragma unroll 1  // sides in turn, not interleaved: fewer live registers
   for (int side = 0; side < 2; ++side) {
-    const R(*cs)[FB] = side == 0 ? cL : cR;
+    const R* cs = (side == 0 ? cL : cR)[f];
     R q[5], dq[3][5];  // global axes
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
+      R cv[VP];
+      lds16(cs + v * VP, cv);
       R s0 = R(0), gD = R(0), g1 = R(0), g2 = R(0);
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        const R c = cs[v * NK + t][f];
+        const R c = cv[t];
         s0 += c * Bt[t];
         if (tmode_p(t) > 0) g1 += c * B1[t];
         if (tmode_q(t) > 0) g2 += c * B2[t];
-        if (t < NN) gD += cs[v * NK + NT + t][f] * Bt[t];
+        if (t < NN) gD += cv[NT + t] * Bt[t];
       }
       q[v] = s0;
       dq[D][v] = gD * sDs[side];
