@@ -185,6 +185,46 @@ def test_sampled_cells_full_size_tgv_256(torch, api, orc):
         assert np.all(err <= RTOL * scale), err / scale
 
 
+def test_fp32_mixed_steps_sampled_full_size_tgv_256(torch, api, orc):
+    """Bench configuration of the timed leg (TGV 256^3, P2, n_q = 3, FP32-mixed, one dghgks_steps call
+    of 2 steps, the second reading the FP32 copy of the state) against the FP64 oracle on sampled
+    cells.  After 2 S2O4 steps (4 stages) a cell depends only on the cells within 4 face-neighbour
+    hops, so the oracle steps a periodic 9^3 box cut around each sampled cell from the same initial
+    state; the box's wrap reaches the centre only after 5 hops, so the centre's result is exact.
+
+    Tolerance, per variable: the FP32 residual of a cell sums a few hundred terms of size up to its
+    absolute-value scale A (the oracle's M^-1 sum |contribution|), so its rounding error is bounded by
+    about 300 u A = 2e-5 A (u = 2^-24); the two steps' increment dt (L(Q^0) + L(Q^1)) + O(dt^2 L_t)
+    carries at most 2.5 such errors in dt A plus 2 in dt^2 A_t."""
+    from paper_2202_13821_b300 import inputs
+
+    n = 256
+    s = api.Solver((n,) * 3, TGV["lo"], TGV["hi"], order=2, mu=1 / 1600, Pr=0.72, n_q=3, precision=1)
+    Q0 = inputs.tgv_state(n, 2, device="cuda")
+    dt = inputs.tgv_dt(n, 2)
+    Qd = Q0.clone()
+    s.steps(Qd, dt, 2)
+    torch.cuda.synchronize()
+    s.status()
+    h = 2 * math.pi / n
+    rng = np.random.default_rng(5)
+    cells = [(0, 0, 0), (255, 255, 255), (131, 7, 200)] + [tuple(int(x) for x in rng.integers(0, n, 3)) for _ in range(5)]
+    worst = np.zeros(5)
+    for (i, j, k) in cells:
+        ix, iy, iz = (torch.tensor((c + np.arange(-4, 5)) % n, device="cuda") for c in (i, j, k))
+        sub = Q0.index_select(2, iz).index_select(3, iy).index_select(4, ix).cpu().numpy()
+        lo = tuple(TGV["lo"][d] + (c - 4) * h for d, c in enumerate((i, j, k)))
+        pb = orc.Problem(order=2, nq=3, n=(9, 9, 9), lo=lo, hi=tuple(x + 9 * h for x in lo), mu=1 / 1600, Pr=0.72)
+        want = orc.step(pb, sub, dt, 2)[:, :, 4, 4, 4]
+        _, _, A, At = orc.residual_cells(pb, sub, dt, np.array([4 + 9 * (4 + 9 * 4)]), scales=True)
+        got = Qd[:, :, k, j, i].cpu().numpy()
+        tol = 2e-5 * (2.5 * dt * A[0].max(axis=1) + 2 * dt * dt * At[0].max(axis=1))
+        err = np.abs(got - want).max(axis=1)
+        assert np.all(err <= tol), (i, j, k, err / tol)
+        worst = np.maximum(worst, err / tol)
+    print("max error / tolerance per variable:", worst)
+
+
 def test_totals_and_kinetic_energy(torch, api, orc):
     from paper_2202_13821_b300 import inputs
 
