@@ -779,13 +779,43 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         }
       }
     };
+    // L2 prefetch of the face-moment blocks a tile's epilogue reads (its cells'
+    // low faces along x, y, z and the high neighbours'), one tile ahead: they
+    // were written by the face kernels long before and are no longer in L2.
+    // (Stage 2 reads only their F_t halves, and ran slower with it.)
+    auto prefetch_faces = [&](long long tt) {
+      const int i0 = (int)(tt % ntx) * CB;
+      const long long r = tt / ntx;
+      const int jj = (int)(r % ny), kk = (int)(r / ny);
+      constexpr int LINES = (10 * NT * (int)sizeof(R) + 127) / 128;  // 128-byte lines per face block
+      for (int e = tid; e < (5 * CB + 1) * LINES; e += nthr) {
+        const int sl = e / LINES, ln = e % LINES;
+        int D, s, hi;
+        if (sl <= CB) {
+          D = 0, s = sl, hi = 0;
+        } else if (sl <= 3 * CB) {
+          D = 1, s = (sl - CB - 1) % CB, hi = (sl - CB - 1) / CB;
+        } else {
+          D = 2, s = (sl - 3 * CB - 1) % CB, hi = (sl - 3 * CB - 1) / CB;
+        }
+        int i = i0 + s;
+        if (i >= nx) i -= nx;
+        if (i >= nx) continue;
+        const int cj = (D == 1 && hi) ? wrapm(jj + 1, ny) : jj, ck = (D == 2 && hi) ? wrapm(kk + 1, nz) : kk;
+        const R* pf = G + ((size_t)D * nc + ((size_t)ck * ny + cj) * nx + i) * (10 * NT) + ln * (128 / sizeof(R));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(pf));
+      }
+    };
     long long t = blockIdx.x, tprev = -1;
     if (t < ntiles) issue(t, 0);
     int b = 0;
     for (; t < ntiles; t += gridDim.x, b ^= 1) {
       cp_async_wait_all();
       __syncthreads();  // tile t staged by all threads; every warp is done with buffer b ^ 1
-      if (t + gridDim.x < ntiles) issue(t + gridDim.x, b ^ 1);
+      if (t + gridDim.x < ntiles) {
+        issue(t + gridDim.x, b ^ 1);
+        if (MODE != MODE_STAGE2) prefetch_faces(t + gridDim.x);
+      }
       if (tprev >= 0) flush(tprev, b ^ 1);
       const R(*coef)[CB];
       if constexpr (std::is_same<Tin, R>::value) {
