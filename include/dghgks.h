@@ -117,6 +117,8 @@ int dghgks_residual(dghgks_ctx* ctx, const double* Q, double dt, double* L, doub
 /* One S2O4 step (Sec. 3, Eq. two-stage), in place on the device state Q:
  *   Q* = Q + dt/2 L(Q) + dt^2/8 L_t(Q)
  *   Q <- Q + dt L(Q) + dt^2/6 (L_t(Q) + 2 L_t(Q*)).
+ * On an FP32-mixed context the stage-1 kernels read Q rounded to FP32 (one
+ * extra elementwise launch rounds it into a library buffer).
  * Asynchronous; consecutive calls on one context must share a stream. */
 int dghgks_step(dghgks_ctx* ctx, double* Q, double dt, void* stream);
 
@@ -124,12 +126,11 @@ int dghgks_step(dghgks_ctx* ctx, double* Q, double dt, void* stream);
  * of one step (8 kernel launches) on `stream`.  The graphs are captured on a
  * private stream at the first call and re-captured when Q, dt or the
  * viscosity (dghgks_set_mu) changes (the executable graph is updated in
- * place when possible).  On an FP32-mixed context the first step reads the
- * FP64 state and every step's state update also writes the state rounded to
- * FP32 into a library buffer, which the stage-1 kernels of the following
- * steps read instead of rounding Q themselves (the same values; a second
- * graph); Q may therefore change between calls but not during one.  Results
- * are identical to nsteps calls of dghgks_step.  Asynchronous.  Must not be
+ * place when possible).  On an FP32-mixed context the stage-1 kernels read the
+ * state rounded to FP32 in a library buffer: the first step of a call rounds Q
+ * into it, and every step's state update writes it for the next step (a
+ * second graph); Q may therefore change between calls but not during one.
+ * Results are identical to nsteps calls of dghgks_step.  Asynchronous.  Must not be
  * called while `stream` itself is being captured.  With profiling on
  * (dghgks_profile) the same launches are enqueued directly, each recorded,
  * instead of replaying the graphs. */

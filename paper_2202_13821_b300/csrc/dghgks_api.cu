@@ -292,6 +292,17 @@ const Ops* select_ops(int precision, int order, int nq) {
   return nullptr;
 }
 
+// The state rounded to FP32 (round to nearest), the input of the stage-1
+// kernels of FP32-mixed steps; n values, two per thread and step.
+__global__ void __launch_bounds__(256) k_round_f32(const double* __restrict__ Q, float* __restrict__ Qf, size_t n) {
+  const size_t n2 = n / 2;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n2; e += (size_t)gridDim.x * blockDim.x) {
+    const double2 q = reinterpret_cast<const double2*>(Q)[e];
+    reinterpret_cast<float2*>(Qf)[e] = make_float2((float)q.x, (float)q.y);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) Qf[n - 1] = (float)Q[n - 1];
+}
+
 template <int NM>
 __global__ void __launch_bounds__(RED_THREADS) k_l2diff_part(const double* __restrict__ A, const double* __restrict__ B,
                                                              int var, const MeshDev m, double* __restrict__ part) {
@@ -334,7 +345,7 @@ int read_flag(dghgks_ctx* c, cudaStream_t s) {
 extern "C" {
 
 static void enqueue_step(dghgks_ctx* c, double* Q, double dt, cudaStream_t s, cudaEvent_t before_write,
-                         bool copy_in = false, bool copy_out = false);
+                         bool have_copy = false, bool copy_out = false);
 
 int dghgks_gauss_rule(int n, double* x, double* w) {
   if (n < 1 || n > 5 || !x || !w) return DGHGKS_EARG;
@@ -517,22 +528,30 @@ int dghgks_step(dghgks_ctx* c, double* Q, double dt, void* stream) {
 
 // Enqueue the 8 launches of one S2O4 step on s.  before_write (may be null): an event that the stage-2
 // cell kernel, the only writer of Q, waits for (readers of Q^n on another
-// stream).  FP32-mixed contexts: copy_in = the stage-1 kernels read the FP32
-// copy Qf of Q^n that the previous step wrote (the values they would convert
-// Q^n to); copy_out = the stage-2 cell kernel writes Qf for the next step.
+// stream).  FP32-mixed contexts: the stage-1 kernels always read the FP32
+// copy Qf of Q^n (one set of kernels for every step, so results never depend
+// on how the steps were grouped into calls); have_copy = the previous step of
+// the same call wrote it, else Q^n is rounded into it first; copy_out = the
+// stage-2 cell kernel writes Qf for the next step.
 static void enqueue_step(dghgks_ctx* c, double* Q, double dt, cudaStream_t s, cudaEvent_t before_write,
-                         bool copy_in, bool copy_out) {
-  copy_in = copy_in && c->Qf;
-  copy_out = copy_out && c->Qf;
-  c->ops->faces(c, copy_in ? c->Qf : Q, copy_in ? FACES_COPY : FACES_FP64, dt, s);
-  c->ops->cell(c, MODE_STAGE1, Q, nullptr, nullptr, dt, s, copy_in, false);  // Q*, inc
+                         bool have_copy, bool copy_out) {
+  const bool copy = c->Qf != nullptr;
+  if (copy && !have_copy) {
+    const size_t n = 5 * (size_t)c->nm * c->ncell;
+    const size_t blocks = (n / 2 + 255) / 256 < 4096 ? (n / 2 + 255) / 256 : 4096;
+    k_round_f32<<<(unsigned)(blocks ? blocks : 1), 256, 0, s>>>(Q, static_cast<float*>(c->Qf), n);
+    c->launches += 1;
+  }
+  c->ops->faces(c, copy ? c->Qf : Q, copy ? FACES_COPY : FACES_FP64, dt, s);
+  c->ops->cell(c, MODE_STAGE1, Q, nullptr, nullptr, dt, s, copy, false);  // Q*, inc
   c->ops->faces(c, c->Qs, FACES_QSTAR, dt, s);
   if (before_write) cudaStreamWaitEvent(s, before_write, 0);
-  c->ops->cell(c, MODE_STAGE2, Q, nullptr, nullptr, dt, s, false, copy_out);  // Q += inc + dt^2/3 L_t(Q*)
+  c->ops->cell(c, MODE_STAGE2, Q, nullptr, nullptr, dt, s, false, copy && copy_out);  // Q += inc + dt^2/3 L_t(Q*)
 }
 
-// Capture (or update) step graph k: one step on Q with the FP64 state (k = 0)
-// or its FP32 copy (k = 1) as the stage-1 input, writing the copy when copy_out.
+// Capture (or update) step graph k: one step on Q, the first of a call (k = 0;
+// on FP32-mixed contexts it rounds Q into the FP32 copy first) or a later one
+// (k = 1, reading the copy the step before wrote), writing the copy when copy_out.
 // The kernels' arguments (state pointer, dt and the gas parameters derived from
 // dt and mu) are baked into the graph: capture again when one changed.
 static int ensure_graph(dghgks_ctx* c, int k, double* Q, double dt, bool copy_out) {
@@ -577,8 +596,8 @@ int dghgks_steps(dghgks_ctx* c, double* Q, double dt, int nsteps, void* stream) 
   if (!c->cap_stream)
     if (int rc = cuda_check(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream"))
       return rc;
-  // the first step reads the FP64 state; on FP32-mixed contexts it and every
-  // later one write the state's FP32 copy, which the later steps read
+  // FP32-mixed contexts: the first step rounds the state into the FP32 copy;
+  // every step's update writes it for the next one, which reads it
   const bool copy = c->Qf && nsteps > 1;
   if (c->prof) {  // profiling: the same launches enqueued directly, each recorded
     for (int n = 0; n < nsteps; ++n) enqueue_step(c, Q, dt, s, nullptr, copy && n > 0, copy);
@@ -590,7 +609,7 @@ int dghgks_steps(dghgks_ctx* c, double* Q, double dt, int nsteps, void* stream) 
     if (int rc = ensure_graph(c, 1, Q, dt, true)) return rc;
   for (int n = 0; n < nsteps; ++n)
     if (int rc = cuda_check(c, cudaGraphLaunch(c->gexec[copy && n > 0 ? 1 : 0], s), "graph launch")) return rc;
-  c->launches += 8 * (int64_t)nsteps;
+  c->launches += 8 * (int64_t)nsteps + (c->Qf && nsteps > 0 ? 1 : 0);  // + the rounding into the copy
   return DGHGKS_OK;
 }
 

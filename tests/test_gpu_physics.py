@@ -193,6 +193,24 @@ def test_fp32_state_copy_stays_within_one_call(torch, api):
     assert not torch.equal(A, B)
 
 
+@pytest.mark.parametrize("order,nq", [(1, 2), (2, 2), (2, 3), (3, 3), (3, 4)])
+def test_fp32_steps_with_state_copy_bitwise_every_layout(torch, api, order, nq):
+    """dghgks_steps (FP32-mixed: later steps read the FP32 copy of the state written by the step
+    before) equals dghgks_step bitwise for every cell-kernel layout: four cells per warp (n_q = 2),
+    a warp per cell (n_q = 3) and two warps per cell (n_q = 4), on a ragged grid."""
+    from paper_2202_13821_b300 import inputs
+
+    n = (19, 6, 5)
+    s = api.Solver(n, **TGV, order=order, mu=1 / 1600, Pr=0.72, n_q=nq, precision=1)
+    Q0 = inputs.tgv_state(n, order, perturb=1e-3, device="cuda")
+    A, B = Q0.clone(), Q0.clone()
+    s.step(A, 3e-3, 3)
+    s.steps(B, 3e-3, 3)
+    s.status()
+    assert torch.equal(A, B)
+    assert not torch.equal(A, Q0)
+
+
 def test_run_host_matches_device_steps(torch, api):
     """dghgks_run_host (host state in and out, E_k of each step on a second stream beside the next
     step) gives bitwise the state and E_k history of device steps with E_k after each."""
