@@ -283,7 +283,7 @@ def run_leg(torch, api, precision, Q0, dt, warmup, steps, barrier, clock=None):
     if clock is not None:
         clock.start()
     e0.record(stream)
-    s.steps(Q, dt, steps)  # FP32-mixed: the state's FP32 copy carries over between the steps
+    s.steps(Q, dt, steps)  # FP32-mixed: the state rounded to FP32 carries over between the steps
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clock.stop() if clock is not None else None
@@ -304,9 +304,8 @@ def algorithmic_bytes(kernel, precision):
     k_face stage 1 reads the state and writes the F and F_t moments; stage 2 reads Q* (flux
     precision) and writes the F_t moments.  k_cell stage 1 reads the state and the moments of its
     faces and writes Q* and inc; stage 2 reads Q*, inc, the F_t moments and the FP64 state and
-    writes the state.  FP32-mixed steps after the first of a dghgks_steps call (the steady state of
-    the timed region) read the state's FP32 copy at stage 1, which stage 2 writes besides the FP64
-    state."""
+    writes the state.  FP32-mixed steps read the state rounded to FP32 at stage 1, which stage 2
+    writes besides the FP64 state (the rounding kernel at the start of a call is not counted)."""
     r = 4 if precision == 1 else 8
     coef, mom = 5 * 10, 10 * 6
     state_in = coef * r  # FP32 copy (FP32-mixed) or the FP64 state
