@@ -293,14 +293,20 @@ const Ops* select_ops(int precision, int order, int nq) {
 }
 
 // The state rounded to FP32 (round to nearest), the input of the stage-1
-// kernels of FP32-mixed steps; n values, two per thread and step.
+// kernels of FP32-mixed steps; n values, two per thread and step when both
+// buffers are 16-byte aligned (VEC), else one.
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_round_f32(const double* __restrict__ Q, float* __restrict__ Qf, size_t n) {
-  const size_t n2 = n / 2;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n2; e += (size_t)gridDim.x * blockDim.x) {
-    const double2 q = reinterpret_cast<const double2*>(Q)[e];
-    reinterpret_cast<float2*>(Qf)[e] = make_float2((float)q.x, (float)q.y);
+  const size_t stride = (size_t)gridDim.x * blockDim.x, e0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (VEC) {
+    for (size_t e = e0; e < n / 2; e += stride) {
+      const double2 q = reinterpret_cast<const double2*>(Q)[e];
+      reinterpret_cast<float2*>(Qf)[e] = make_float2((float)q.x, (float)q.y);
+    }
+    if (e0 == 0 && (n & 1)) Qf[n - 1] = (float)Q[n - 1];
+  } else {
+    for (size_t e = e0; e < n; e += stride) Qf[e] = (float)Q[e];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) Qf[n - 1] = (float)Q[n - 1];
 }
 
 template <int NM>
@@ -539,7 +545,11 @@ static void enqueue_step(dghgks_ctx* c, double* Q, double dt, cudaStream_t s, cu
   if (copy && !have_copy) {
     const size_t n = 5 * (size_t)c->nm * c->ncell;
     const size_t blocks = (n / 2 + 255) / 256 < 4096 ? (n / 2 + 255) / 256 : 4096;
-    k_round_f32<<<(unsigned)(blocks ? blocks : 1), 256, 0, s>>>(Q, static_cast<float*>(c->Qf), n);
+    const unsigned grid = (unsigned)(blocks ? blocks : 1);
+    if (((uintptr_t)Q | (uintptr_t)c->Qf) % 16 == 0)
+      k_round_f32<true><<<grid, 256, 0, s>>>(Q, static_cast<float*>(c->Qf), n);
+    else  // the caller's state need only be 8-byte aligned
+      k_round_f32<false><<<grid, 256, 0, s>>>(Q, static_cast<float*>(c->Qf), n);
     c->launches += 1;
   }
   c->ops->faces(c, copy ? c->Qf : Q, copy ? FACES_COPY : FACES_FP64, dt, s);

@@ -211,6 +211,25 @@ def test_fp32_steps_with_state_copy_bitwise_every_layout(torch, api, order, nq):
     assert not torch.equal(A, Q0)
 
 
+def test_fp32_steps_on_an_8_byte_aligned_state(torch, api):
+    """The C ABI takes any contiguous FP64 state: a view that starts one value into its storage (8-byte,
+    not 16-byte aligned) steps to the same result as an aligned copy."""
+    from paper_2202_13821_b300 import inputs
+
+    n = (12, 5, 4)
+    s = api.Solver(n, **TGV, order=2, mu=1 / 1600, Pr=0.72, n_q=3, precision=1)
+    Q0 = inputs.tgv_state(n, 2, perturb=1e-3, device="cuda")
+    buf = torch.empty(Q0.numel() + 1, dtype=torch.float64, device="cuda")
+    V = buf[1:].view(Q0.shape)
+    V.copy_(Q0)
+    assert V.data_ptr() % 16 == 8
+    A = Q0.clone()
+    s.steps(A, 3e-3, 2)
+    s.steps(V, 3e-3, 2)
+    s.status()
+    assert torch.equal(A, V)
+
+
 def test_run_host_matches_device_steps(torch, api):
     """dghgks_run_host (host state in and out, E_k of each step on a second stream beside the next
     step) gives bitwise the state and E_k history of device steps with E_k after each."""
