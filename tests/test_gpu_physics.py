@@ -169,9 +169,9 @@ def test_deterministic_and_graph_replay_bitwise(torch, api):
 
 def test_fp32_state_copy_stays_within_one_call(torch, api):
     """FP32-mixed dghgks_steps: the steps after the first read the FP32 copy of the state that the
-    step before wrote; the first step of every call reads the FP64 state, so a state changed between
-    calls is what the next call steps, and a profiled call (launches enqueued directly, each
-    recorded) gives the graph replay's result."""
+    step before wrote; the first step of every call rounds the FP64 state into it afresh, so a
+    state changed between calls is what the next call steps, and a profiled call (launches enqueued
+    directly, each recorded) gives the graph replay's result."""
     from paper_2202_13821_b300 import inputs
 
     s = api.Solver((20, 12, 9), **TGV, order=2, mu=1 / 1600, Pr=0.72, precision=1)
