@@ -142,16 +142,23 @@ constexpr int FB = 32;  // faces per CTA in k_face
 // four sub-partitions (16384 registers each) and a CTA's warps are spread
 // over them, so the cap for C resident CTAs of W warps is
 // 16384 / (ceil(C W / 4) x 32), rounded down to a multiple of 8.
-// FP32: 3 CTAs of 9 warps (n_q = 3; 72 registers: more spills than 2 CTAs at
-// 96, but the extra warps hide them -- 2-7% faster per direction at 256^3),
-// 4 CTAs of 4 warps (n_q = 2; 128 registers) or 1 CTA of 16 warps (n_q = 4; 128).
+// FP32: 5 CTAs of 3 warps (n_q = 3; 128 registers, no spills -- at 256^3 each
+// direction is 3-6% faster than 4 CTAs at 156 registers and 20% faster than
+// 8 CTAs at 80 registers, which spill), 4 CTAs of 4 warps (n_q = 2; 128
+// registers) or 1 CTA of 16 warps (n_q = 4; 128).
 // FP64 (bound by the FP64 pipe): 1 CTA.
 #ifndef FACE_CTAS_NQ3
-#define FACE_CTAS_NQ3 3
+#define FACE_CTAS_NQ3 5
 #endif
+// Gauss points per thread: FP32 at n_q = 3 loops over a row of NQ points (3
+// warps per CTA, many CTAs per SM), otherwise one point per thread.
+template <class R, int NQ>
+constexpr int face_ppt() {
+  return (sizeof(R) == 4 && NQ == 3) ? NQ : 1;
+}
 template <class R, int NQ>
 constexpr int face_max_regs() {
-  constexpr int warps = (FB * NQ * NQ + 31) / 32;
+  constexpr int warps = (FB * NQ * NQ / face_ppt<R, NQ>() + 31) / 32;
   constexpr int ctas = sizeof(R) == 4 ? (NQ == 2 ? 4 : NQ == 3 ? FACE_CTAS_NQ3 : 1) : 1;
   constexpr int per_part = (warps * ctas + 3) / 4;
   constexpr int cap = 16384 / (per_part * 32) / 8 * 8;
@@ -169,6 +176,7 @@ template <class R, int ORDER, int NQ>
 struct FaceSmem {
   static constexpr int NM = n_modes(ORDER), NT = n_tmodes(ORDER), NN = n_tmodes(ORDER - 1), NK = NT + NN;
   static constexpr int NP = NQ * NQ, W16 = 16 / sizeof(R);
+  static constexpr int PPT = face_ppt<R, NQ>(), THREADS = FB * NP / PPT;  // points per thread, CTA size
   static constexpr int VP = (NK + W16 - 1) / W16 * W16;
   static constexpr int PITCH = ((5 * VP / W16) % 2 == 1) ? 5 * VP : 5 * VP + W16;
   static constexpr size_t coef = sizeof(R) * PITCH * FB;  // one side
@@ -203,11 +211,12 @@ __device__ __forceinline__ int wrapm(int i, int n) { return i < 0 ? i + n : (i >
 // FTO (the stage-2 pass of S2O4, which needs L_t(Q*) only): the F_t moments
 // alone are projected and stored; F is left to dead-code elimination.
 template <class R, int ORDER, int NQ, int D, class Tin, bool FTO = false>
-__global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>()))
+__global__ void __launch_bounds__(FaceSmem<R, ORDER, NQ>::THREADS) __maxnreg__((face_max_regs<R, NQ>()))
     k_face(const Tin* __restrict__ Q, R* __restrict__ G, const GasPar<R> gp, const MeshDev m,
            unsigned* __restrict__ flag) {
   using S = FaceSmem<R, ORDER, NQ>;
   constexpr int NM = S::NM, NT = S::NT, NN = S::NN, NP = S::NP, VP = S::VP, PITCH = S::PITCH;
+  constexpr int PPT = S::PPT, NTHR = S::THREADS, NPW = NP / PPT;  // NPW threads per face
   constexpr int T1 = tan1(D), T2 = tan2(D);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R(*cL)[PITCH] = reinterpret_cast<R(*)[PITCH]>(smem_raw);  // [face][var VP + poly value]
@@ -215,7 +224,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   R(*Fs)[NP][FB] = reinterpret_cast<R(*)[NP][FB]>(smem_raw + 2 * S::coef);
 
   const int tid = threadIdx.x;
-  const int f = tid % FB, p = tid / FB;
+  const int f = tid % FB, pw = tid / FB;
   const int i0 = blockIdx.x * FB, j = blockIdx.y, k = blockIdx.z;
   const int nx = m.nx, ny = m.ny, nz = m.nz;
   const long long nc = m.ncell;
@@ -223,7 +232,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   // stage the face polynomials of the left (-e_D; traces at r_D = +1) and
   // right (r_D = -1) cells of each face: P_n(+1) = 1, P_n(-1) = (-1)^n,
   // P'_n(+1) = n(n+1)/2, P'_n(-1) = (-1)^(n+1) n(n+1)/2
-  for (int e = tid; e < 2 * 5 * FB; e += FB * NP) {
+  for (int e = tid; e < 2 * 5 * FB; e += NTHR) {
     const int ff = e % FB, rest = e / FB, v = rest % 5, side = rest / 5;
     const int i = i0 + ff;
     R Vt[NT], Nt[NN];
@@ -261,6 +270,17 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
 
   const int i = i0 + f;
   const bool active = i < nx;
+  // gradient scales: along D those of the left and right cells, tangential
+  // ones shared by both cells (rectilinear mesh)
+  const int ic = active ? i : 0;
+  const int cidx[3] = {ic, j, k};
+  const int nAx = D == 0 ? nx : (D == 1 ? ny : nz);
+  const R sDs[2] = {cell_sc<R>(m, D, wrapm(cidx[D] - 1, nAx)), cell_sc<R>(m, D, cidx[D])};
+  const R s1 = cell_sc<R>(m, T1, cidx[T1]), s2 = cell_sc<R>(m, T2, cidx[T2]);
+  const R area = face_area<R>(m, D, cidx[T1], cidx[T2]);
+#pragma unroll 1
+  for (int pp = 0; pp < PPT; ++pp) {
+  const int p = pw * PPT + pp;  // this thread's Gauss point of the face
   const int a = p / NQ, b = p % NQ;
   const R xa = gauss_xr<R>(NQ, a), xb = gauss_xr<R>(NQ, b);
   // tangential basis at this point: phi_t, d phi_t / d r_1, d phi_t / d r_2
@@ -272,13 +292,6 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
     B1[t] = tp > 0 ? dleg<R>(tp, xa) * leg<R>(tq, xb) : R(0);
     B2[t] = tq > 0 ? leg<R>(tp, xa) * dleg<R>(tq, xb) : R(0);
   }
-  // gradient scales: along D those of the left and right cells, tangential
-  // ones shared by both cells (rectilinear mesh)
-  const int ic = active ? i : 0;
-  const int cidx[3] = {ic, j, k};
-  const int nAx = D == 0 ? nx : (D == 1 ? ny : nz);
-  const R sDs[2] = {cell_sc<R>(m, D, wrapm(cidx[D] - 1, nAx)), cell_sc<R>(m, D, cidx[D])};
-  const R s1 = cell_sc<R>(m, T1, cidx[T1]), s2 = cell_sc<R>(m, T2, cidx[T2]);
 
   // Each side in turn: traces of the left cell (side 0) or the right cell
   // (side 1) from its face polynomials, rotated to the local frame (axes D,
@@ -331,7 +344,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   R Fl[5], Ftl[5];
   ok = iface_finish(sums, gp, Fl, Ftl) && ok;
   if (active && !ok) atomicOr(flag, 1u);
-  const R w = active ? gauss_wr<R>(NQ, a) * gauss_wr<R>(NQ, b) * face_area<R>(m, D, cidx[T1], cidx[T2]) : R(0);
+  const R w = active ? gauss_wr<R>(NQ, a) * gauss_wr<R>(NQ, b) * area : R(0);
   if (!FTO) {
     Fs[0][p][f] = w * Fl[0];
     Fs[1 + A0][p][f] = w * Fl[1];
@@ -344,6 +357,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   Fs[6 + A1][p][f] = w * Ftl[2];
   Fs[6 + A2][p][f] = w * Ftl[3];
   Fs[9][p][f] = w * Ftl[4];
+  }
   __syncthreads();
 
   // tangential projection G[D][face][c][t] = sum_p Fs[c][p] phi_t(p): the
@@ -353,7 +367,7 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   // shared memory (over the coefficient staging area, free after the
   // barrier above) and written as one contiguous block.
   R(*Gs)[10][NT] = reinterpret_cast<R(*)[10][NT]>(smem_raw);
-  for (int c = (FTO ? 5 : 0) + p; c < 10; c += NP) {
+  for (int c = (FTO ? 5 : 0) + pw; c < 10; c += NPW) {
     R fv[NP];
 #pragma unroll
     for (int pp = 0; pp < NP; ++pp) fv[pp] = Fs[c][pp][f];
@@ -371,12 +385,12 @@ __global__ void __launch_bounds__(FB* NQ* NQ) __maxnreg__((face_max_regs<R, NQ>(
   R* const dst = G + ((size_t)D * nc + ((size_t)k * ny + j) * nx + i0) * (10 * NT);
   const R* const src = &Gs[0][0][0];
   if (FTO) {
-    for (int e = tid; e < nf * 5 * NT; e += FB * NP) {
+    for (int e = tid; e < nf * 5 * NT; e += NTHR) {
       const int ff = e / (5 * NT), r = e % (5 * NT);
       dst[ff * (10 * NT) + 5 * NT + r] = src[ff * (10 * NT) + 5 * NT + r];
     }
   } else {
-    for (int e = tid; e < nf * 10 * NT; e += FB * NP) dst[e] = src[e];
+    for (int e = tid; e < nf * 10 * NT; e += NTHR) dst[e] = src[e];
   }
 }
 

@@ -188,7 +188,7 @@ struct Impl {
     const GasPar<R> g = gas_par<R>(c, dt);
     const MeshDev m = mesh_dev(c);
     dim3 grid((c->n[0] + FB - 1) / FB, c->n[1], c->n[2]);
-    dim3 block(FB * NQ * NQ);
+    dim3 block(FS::THREADS);
     R* G = static_cast<R*>(c->G);
     {
       ProfScope ps(c, 0, s);

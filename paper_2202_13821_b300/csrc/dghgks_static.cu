@@ -86,7 +86,7 @@ void launch(const MeshDev& m, const GasPar<R>& g, const double* Q, double* L, do
             double dt, cudaStream_t s) {
   using FS = FaceSmem<R, ORDER, NQ>;
   using LY = CellLayout<ORDER, NQ>;
-  const dim3 fgrid((m.nx + FB - 1) / FB, m.ny, m.nz), fblock(FB * NQ * NQ);
+  const dim3 fgrid((m.nx + FB - 1) / FB, m.ny, m.nz), fblock(FS::THREADS);
   k_face<R, ORDER, NQ, 0, double><<<fgrid, fblock, FS::bytes, s>>>(Q, G, g, m, flag);
   k_face<R, ORDER, NQ, 1, double><<<fgrid, fblock, FS::bytes, s>>>(Q, G, g, m, flag);
   k_face<R, ORDER, NQ, 2, double><<<fgrid, fblock, FS::bytes, s>>>(Q, G, g, m, flag);
