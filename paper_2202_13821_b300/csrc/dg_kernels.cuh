@@ -142,24 +142,24 @@ constexpr int FB = 32;  // faces per CTA in k_face
 // four sub-partitions (16384 registers each) and a CTA's warps are spread
 // over them, so the cap for C resident CTAs of W warps is
 // 16384 / (ceil(C W / 4) x 32), rounded down to a multiple of 8.
-// FP32: 5 CTAs of 3 warps (n_q = 3; 128 registers, no spills -- at 256^3 each
-// direction is 3-6% faster than 4 CTAs at 156 registers and 20% faster than
-// 8 CTAs at 80 registers, which spill), 4 CTAs of 4 warps (n_q = 2; 128
-// registers) or 1 CTA of 16 warps (n_q = 4; 128).
-// FP64 (bound by the FP64 pipe): 1 CTA.
+// FP32: a thread takes the NQ Gauss points of one row of its face in turn
+// (NQ warps per CTA), and the CTAs per SM are chosen so that 128 registers
+// hold the kernel without spills: 8 CTAs at n_q = 2, 5 at n_q = 3, 4 at
+// n_q = 4.  At 256^3, n_q = 3, a face launch took 3-6% longer with 4 CTAs
+// at 156 registers, 22% longer with 8 CTAs at 80 registers (spills) and 24%
+// longer with one warp per Gauss point (9 warps, 72 registers, spills).
+// FP64 (bound by the FP64 pipe): one warp per Gauss point, 1 CTA.
 #ifndef FACE_CTAS_NQ3
 #define FACE_CTAS_NQ3 5
 #endif
-// Gauss points per thread: FP32 at n_q = 3 loops over a row of NQ points (3
-// warps per CTA, many CTAs per SM), otherwise one point per thread.
 template <class R, int NQ>
 constexpr int face_ppt() {
-  return (sizeof(R) == 4 && NQ == 3) ? NQ : 1;
+  return (sizeof(R) == 4 && NQ >= 2) ? NQ : 1;
 }
 template <class R, int NQ>
 constexpr int face_max_regs() {
   constexpr int warps = (FB * NQ * NQ / face_ppt<R, NQ>() + 31) / 32;
-  constexpr int ctas = sizeof(R) == 4 ? (NQ == 2 ? 4 : NQ == 3 ? FACE_CTAS_NQ3 : 1) : 1;
+  constexpr int ctas = sizeof(R) == 4 ? (NQ == 2 ? 8 : NQ == 3 ? FACE_CTAS_NQ3 : 4) : 1;
   constexpr int per_part = (warps * ctas + 3) / 4;
   constexpr int cap = 16384 / (per_part * 32) / 8 * 8;
   return cap > 255 ? 255 : cap;
