@@ -138,6 +138,33 @@ def test_p3_residual(torch, api, orc, nq, state):
     assert_residual_parity(L, Lt, ref)
 
 
+@pytest.mark.parametrize("order,nq", [(1, 2), (2, 2), (2, 3), (3, 3), (3, 4)])
+def test_fp32_mixed_residual_every_layout(torch, api, orc, order, nq):
+    """FP32-mixed residual (Sec. 3, Eq. (flux) and (flux-2) in FP32 arithmetic) against the FP64
+    oracle for every FP32 face layout (a thread per row of n_q Gauss points) and cell layout, on a
+    perturbed Taylor-Green state with 35 cells along x (one full 32-face CTA and a ragged one).
+
+    Bound per variable: 2e-5 of the oracle's magnitude scale (the sum of the absolute values of the
+    terms that make up the residual).  FP32 rounds each of the few hundred terms of a point flux and
+    of the projections to 6e-8 of its size; 2e-5 = 335 units of FP32 rounding of the scale leaves
+    room for their accumulation and for the divisions and exponentials of the flux.  Measured on a
+    B300: L within 2.5e-7 of its scale for every layout; L_t, formed from the time fit of the face
+    flux, within 1.6e-5 at P1 (the fewest terms per scale), 9e-6 at P2 and 5e-6 at P3."""
+    from paper_2202_13821_b300 import inputs
+
+    n = (35, 5, 3)
+    s, pb = make(api, orc, n, order=order, nq=nq, mu=1 / 1600, Pr=0.72, precision=1, **TGV)
+    Q = inputs.modal_state(inputs.tgv_prim, n, order, TGV["lo"], TGV["hi"], perturb=1e-3)
+    L, Lt, ref = residual_pair(torch, s, pb, orc, Q, 1.5e-3)
+    worst = []
+    for a, b, sc in ((L, ref[0], ref[2]), (Lt, ref[1], ref[3])):
+        err = np.abs(a - b).reshape(5, -1).max(axis=1)
+        scale = np.abs(sc).reshape(5, -1).max(axis=1)
+        worst.append((err / scale).max())
+        assert np.all(err <= 2e-5 * scale), err / scale
+    print(f"P{order} n_q={nq}: max err / scale L {worst[0]:.2e}, L_t {worst[1]:.2e}")
+
+
 @pytest.mark.parametrize("order,nq,case", [(1, 2, "adv"), (2, 3, "tgv"), (3, 4, "tgv")])
 def test_s2o4_step_parity(torch, api, orc, order, nq, case):
     from paper_2202_13821_b300 import inputs
