@@ -232,13 +232,17 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
-    """Hash of the forward kernel sources; a profile summary is valid only for the same hash."""
+    """Hash of the forward kernel sources and of their compiler options; a profile summary is valid
+    only for the same hash."""
     import hashlib
+
+    from paper_2202_13821_b300 import build
 
     h = hashlib.sha1()
     for f in ("dg_kernels.cuh", "gks_point.cuh", "dg_tables.cuh"):
         with open(os.path.join(ROOT, "paper_2202_13821_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
+    h.update(" ".join(build.NVCC_FLAGS + build.EXTRA.get("dghgks_api.cu", [])).encode())
     return h.hexdigest()[:12]
 
 
