@@ -11,13 +11,8 @@ ROOT = os.path.dirname(HERE)
 SO = os.path.join(HERE, "libdghgks.so")
 SOURCES = [os.path.join(HERE, "csrc", "dghgks_api.cu"), os.path.join(HERE, "csrc", "dghgks_static.cu"),
            os.path.join(HERE, "csrc", "dghgks_adjoint.cu")]
-# Forward kernels: FP32 arithmetic flushes denormals to zero and takes the
-# approximate division and square root for the operations that do not already
-# use the special-function intrinsics (about 2 ulp; FP64 arithmetic is not
-# affected).  At 256^3 P2 the face launches run 2.5 % faster.
-FP32_FAST = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
 # extra device-compiler options per source (see the header of dghgks_adjoint.cu)
-EXTRA = {"dghgks_api.cu": FP32_FAST, "dghgks_static.cu": FP32_FAST, "dghgks_adjoint.cu": ["-Xptxas", "-O1"]}
+EXTRA = {"dghgks_adjoint.cu": ["-Xptxas", "-O1"]}
 DEPS = [os.path.abspath(__file__)] + SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc")) if f.endswith((".cu", ".cuh"))] + [
     os.path.join(ROOT, "include", "dghgks.h")]
 

@@ -39,9 +39,12 @@ using std::exp;
 using std::sqrt;
 
 // Division, reciprocal square root and exponential.  The FP64 path uses the
-// IEEE operations; the FP32 path uses the single-instruction approximations
-// of the special-function unit (about 2 ulp), which is well inside the
-// FP32-mixed error budget and avoids the multi-instruction IEEE sequences.
+// IEEE operations; the FP32 path uses the approximate PTX instructions of the
+// special-function unit with denormal inputs and results flushed to zero
+// (about 2 ulp; the exponential as 2^(x log2 e), whose error grows with |x|
+// as the product is rounded), which is well inside the FP32-mixed error
+// budget and avoids the multi-instruction IEEE sequences and the extra
+// instructions that the denormal-preserving forms need.
 template <class R>
 DG_HD R fdiv(R a, R b) {
   return a / b;
@@ -57,15 +60,22 @@ DG_HD R fexp(R x) {
 #ifdef __CUDA_ARCH__
 template <>
 __device__ __forceinline__ float fdiv<float>(float a, float b) {
-  return __fdividef(a, b);
+  float r;
+  asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
 }
 template <>
 __device__ __forceinline__ float frsqrt<float>(float x) {
-  return rsqrtf(x);
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 template <>
 __device__ __forceinline__ float fexp<float>(float x) {
-  return __expf(x);
+  // e^x = 2^(x log2 e)
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x * 1.4426950408889634f));
+  return r;
 }
 #endif
 
