@@ -501,13 +501,16 @@ struct StageIO {
 // Resident CTAs of k_cell per SM requested from the compiler (FP32): 2 gives
 // the register cap 128; the stage-2 pass (L_t only) runs 4 (cap 64; at most a
 // few dozen bytes of spills for n_q <= 3), whose extra warps hide the latency
-// of its face-moment reads (3-6 % faster than 3 CTAs at cap 80).
+// of its face-moment reads (3-6 % faster than 3 CTAs at cap 80).  At n_q = 4
+// (two warps per cell) every pass runs 3 (cap 80, no spills): 17-21 % faster
+// than 2 at 128^3 P3; at n_q = 3 three CTAs made stage 1 slower (P3) or no
+// faster (P2).
 #ifndef CELL_MIN_CTAS_F32
 #define CELL_MIN_CTAS_F32 2
 #endif
 template <class R, int NQ, int MODE>
 constexpr int cell_min_ctas() {
-  return sizeof(R) == 4 ? (MODE == 2 && NQ <= 3 ? 4 : CELL_MIN_CTAS_F32) : 1;
+  return sizeof(R) == 4 ? (MODE == 2 && NQ <= 3 ? 4 : (NQ == 4 ? 3 : CELL_MIN_CTAS_F32)) : 1;
 }
 template <class R, int ORDER, int NQ, int MODE, class Tin>
 __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_ctas<R, NQ, MODE>()))
