@@ -14,10 +14,13 @@ State layout everywhere: ``Q[var][mode][z][y][x]`` float64, var = (rho, rho U,
 rho V, rho W, rho E), modes of P_k ordered by total degree with pure powers
 first (Sec. 3, Eq. expansion).
 
-Parity status: every function is pinned by ``tests/test_oracle_*.py`` except
-the Prandtl-number correction's time-derivative term (Pr != 1), which the
-paper does not define: PARITY UNPINNED for that term (its F part is pinned
-by the Navier-Stokes limit).
+Parity status: every function is pinned by ``tests/test_oracle_*.py``.  The
+interface flux of Eq. (flux) is pinned at continuous states by its Euler and
+Navier-Stokes limits and at discontinuous states by a brute-force
+velocity/time quadrature of the distribution it integrates
+(``tests/test_oracle_flux_quadrature.py``).  The Prandtl-number correction
+(Pr != 1) is a reading, since the paper does not define it; its F and F_t
+arithmetic is pinned by that same quadrature of the definition taken.
 """
 from __future__ import annotations
 

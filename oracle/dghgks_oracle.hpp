@@ -37,8 +37,11 @@
 //     weights); the difference T(dt) - 2 T(dt/2) is evaluated in factored form.
 //   * Prandtl number: Pr != 1 adds (1/Pr - 1) q to the energy flux, with
 //     q = 1/2 <(u_n - U_n)(|u-U|^2 + xi^2) f> the heat flux of the same f
-//     (not in the paper, whose Taylor-Green case has Pr = 1).  PARITY
-//     UNPINNED: the paper fixes no value for this term.
+//     (not in the paper, whose Taylor-Green case has Pr = 1).  The definition
+//     is a reading: the paper fixes no value for this term.  Its arithmetic is
+//     pinned: F against the Navier-Stokes heat flux at continuous states, F
+//     and F_t against a brute-force velocity/time quadrature of the same
+//     definition at discontinuous states (tests/test_oracle_flux_quadrature.py).
 #pragma once
 #include <cmath>
 #include <cstdint>

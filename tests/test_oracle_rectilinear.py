@@ -141,12 +141,12 @@ def test_shear_wave_viscous_decay_on_mapped_mesh(orc, axis):
     assert e3 < 5e-3, e3
 
 
-def _advection_error_mapped(orc, order, n, T=0.1):
+def _advection_error_mapped(orc, order, n, T=0.1, nq=None):
     nodes = tuple(inputs.mapped_nodes(n) for _ in range(3))
     hmin = min(np.diff(nodes[0]))
     dt0 = 0.1 * hmin / (math.sqrt(3) + math.sqrt(1.4 / 0.8))
     ns = math.ceil(T / dt0)
-    pb = orc.Problem(order=order, nq=order + 1, n=(n, n, n), tau_eps=0.01, nodes=nodes)
+    pb = orc.Problem(order=order, nq=order + 1 if nq is None else nq, n=(n, n, n), tau_eps=0.01, nodes=nodes)
     Q = orc.project(pb, orc.IC_ADVECTION, (0.2, 0.0))
     Q = orc.step(pb, Q, T / ns, ns)
     return orc.density_errors(pb, Q, orc.IC_ADVECTION, (0.2, T))
@@ -161,9 +161,17 @@ def test_advection_convergence_on_mapped_mesh(orc, order, n0, min_order):
     assert orders[0] > min_order and orders[1] > min_order, orders
 
 
-def test_golden_nonuniform_orders_fixture_is_k_plus_1():
+@pytest.mark.slow
+def test_mapped_mesh_order_matches_paper_table(orc):
+    """P2 with the paper's Gauss rule (n_q = k) on the mapped mesh: the L2 order from 8^3 to 16^3
+    is the expected 3 and agrees with the finest order of the paper's table for this mesh (Sec. 5.1,
+    Table tab-3d-3, held in tests/golden/advection_orders_nonuniform.txt; measured 3.03 against
+    3.0864).  The P3 row (measured 3.97 against 4.0015) is left out to keep the CPU suite short;
+    the uniform-mesh test covers P3."""
     rows = [l.split() for l in open(os.path.join(HERE, "golden", "advection_orders_nonuniform.txt")) if l[0] != "#"]
-    assert len(rows) == 2
-    for k, expect, finest in rows:
-        assert int(expect) == int(k) + 1
-        assert abs(float(finest) - (int(k) + 1)) < 0.1
+    k, expected, finest = next((int(a), int(b), float(c)) for a, b, c in rows if a == "2")
+    e0 = _advection_error_mapped(orc, k, 8, nq=k)
+    e1 = _advection_error_mapped(orc, k, 16, nq=k)
+    l2_order = math.log2(e0[1] / e1[1])
+    assert l2_order > expected - 0.1, l2_order
+    assert abs(l2_order - finest) < 0.15, (l2_order, finest)

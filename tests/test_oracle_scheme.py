@@ -7,7 +7,9 @@
 * optimal order k+1 on the 3D density advection against its exact solution,
   with rho = 1 + 0.2 sin(pi(x+y+z-3t)) (U = V = W = 1; the printed "-t" is
   inconsistent with the unit velocities, and the test shows the scheme does
-  not approach it);
+  not approach it), from 8^3 to 16^3 cells; with the paper's Gauss rule
+  (n_q = k) the measured L2 order matches the finest order the paper prints
+  (Sec. 5.1, Tables tab-3d-1/2, held in tests/golden/advection_orders.txt);
 * Taylor-Green vortex: E_k(0) = 1/8 for rho = 1 (closed form of the initial
   field), and dE_k/dt < 0.
 """
@@ -62,26 +64,54 @@ def test_s2o4_scalar_is_fourth_order_taylor(orc, lam, dt):
     assert abs(orc.s2o4_scalar(lam, 1.0, dt) - want) < 1e-15
 
 
-def _advection_error(orc, order, n, T=0.1, t_exact=None):
+def _advection_state(orc, order, n, T=0.1, nq=None):
     h = 2.0 / n
     dt0 = 0.1 * h / (math.sqrt(3) + math.sqrt(1.4 / 0.8))  # CFL 0.1 with max(|U| + c)
     ns = math.ceil(T / dt0)
-    pb = orc.Problem(order=order, nq=order + 1, n=(n, n, n), tau_eps=0.01)
+    pb = orc.Problem(order=order, nq=order + 1 if nq is None else nq, n=(n, n, n), tau_eps=0.01)
     Q = orc.project(pb, orc.IC_ADVECTION, (0.2, 0.0))
-    Q = orc.step(pb, Q, T / ns, ns)
-    return orc.density_errors(pb, Q, orc.IC_ADVECTION, (0.2, T if t_exact is None else t_exact))
+    return pb, orc.step(pb, Q, T / ns, ns)
+
+
+def _advection_error(orc, order, n, T=0.1, nq=None):
+    pb, Q = _advection_state(orc, order, n, T, nq)
+    return orc.density_errors(pb, Q, orc.IC_ADVECTION, (0.2, T))
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("order,n0,min_order", [(1, 8, 1.85), (2, 4, 2.6)])
+@pytest.mark.parametrize("order,n0,min_order", [(1, 8, 1.9), (2, 8, 2.9)])
 def test_advection_convergence_order(orc, order, n0, min_order):
-    e0 = _advection_error(orc, order, n0)
-    e1 = _advection_error(orc, order, 2 * n0)
+    # measured (L1, L2) orders from 8^3 to 16^3: P1 2.06, 1.97; P2 (n_q = 3) 3.06, 2.98
+    T = 0.1
+    e0 = _advection_error(orc, order, n0, T)
+    pb, Q1 = _advection_state(orc, order, 2 * n0, T)
+    e1 = orc.density_errors(pb, Q1, orc.IC_ADVECTION, (0.2, T))
     orders = np.log2(e0 / e1)
     assert orders[0] > min_order and orders[1] > min_order, orders
     # the printed exact solution with "-t" is not approached
-    bad = _advection_error(orc, order, 2 * n0, t_exact=0.1 / 3)
+    bad = orc.density_errors(pb, Q1, orc.IC_ADVECTION, (0.2, T / 3))
     assert bad[1] > 20 * e1[1]
+
+
+def golden_orders(name):
+    """Rows (order k, expected order, finest L2 order the paper prints) of a golden fixture."""
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", name)) if l[0] != "#"]
+    return [(int(k), int(e), float(f)) for k, e, f in rows]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("row", golden_orders("advection_orders.txt"), ids=lambda r: f"P{r[0]}")
+def test_advection_order_matches_paper_table(orc, row):
+    """With the paper's Gauss rule (n_q = k, Sec. 3 Remark 2) the L2 order from 8^3 to 16^3 is the
+    expected k+1 and agrees with the finest order of the paper's tables (measured: P2 3.04 against
+    3.0821, P3 3.99 against 3.9962); the error values themselves depend on the unprinted final time
+    and time step and are not compared."""
+    k, expected, finest = row
+    e0 = _advection_error(orc, k, 8, nq=k)
+    e1 = _advection_error(orc, k, 16, nq=k)
+    l2_order = math.log2(e0[1] / e1[1])
+    assert l2_order > expected - 0.1, l2_order
+    assert abs(l2_order - finest) < 0.15, (l2_order, finest)
 
 
 def vortex_errors(orc, order, n, T=1.0, cfl=0.1):
@@ -102,13 +132,6 @@ def test_isotropic_vortex_p1_order(orc):
     e0, e1 = vortex_errors(orc, 1, 20), vortex_errors(orc, 1, 40)
     orders = np.log2(e0 / e1)
     assert orders[1] > 1.7, orders  # L2 order ~ k+1 = 2
-
-
-def test_golden_orders_fixture_is_k_plus_1():
-    rows = [l.split() for l in open(os.path.join(HERE, "golden", "advection_orders.txt")) if l[0] != "#"]
-    for k, expect, finest in rows:
-        assert int(expect) == int(k) + 1
-        assert abs(float(finest) - (int(k) + 1)) < 0.1
 
 
 def test_tgv_initial_enstrophy_dissipation(orc):
