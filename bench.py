@@ -8,16 +8,23 @@ CFL 0.15.  A step is one S2O4 time step = two full residual stages over the
 whole grid (3 face launches + 1 cell launch per stage).
 
 Metric: DOF-stage-updates/s = 5 * N_modes * N_cells * 2 / (time per step),
-whole job (sum over ranks).  The headline value is the FP32-mixed path (flux
-and quadrature in FP32, stage accumulation and reductions in FP64); the FP64
-path is measured on the same state and reported beside it, with the error
-of FP32-mixed against FP64 (L2 density difference, relative kinetic-energy
-history difference).
+whole job (sum over ranks).  The headline value is the FP32-mixed path, timed
+as a user runs it: one dghgks_steps call of K steps (CUDA-graph replay) between
+two CUDA events, after W untimed steps; per-kernel times for the roofline come
+from a separate profiled pass.  Beside it: the FP32 flux with FP64 stage
+arithmetic and the FP64 path on the same state, the errors of the FP32 paths
+against FP64 (L2 density difference, relative kinetic-energy history) and
+against the oracle (the oracle steps 9^3 boxes cut around sampled cells; that
+is also the CPU baseline), the end-to-end rate through dghgks_run_host with
+host buffers, the measured FMA and transcendental rates of the GPU, and the
+adjoint leg (Taylor-Green 64^3 P2 FP64, 100 checkpointed steps).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
 --impl reference times the FP64 CPU oracle (the method written plainly from
-the paper) on a bounded sample of cells of the same workload.
+the paper): each step is a whole S2O4 step of the oracle on a periodic 16^3
+Taylor-Green grid (P2, n_q = 3), the workload at a size the host cores step
+in seconds.
 Multi-GPU: one replica per rank ("replicas only": independent problems, no
 data-path collective), weak scaling; barrier + max over ranks for timing.
 """
@@ -41,8 +48,6 @@ UNIT = "DOF-stage-updates/s"
 N_CELLS_1D = 256
 ORDER, NQ = 2, 3
 MU, PR, GAMMA, MA = 1.0 / 1600.0, 0.72, 1.4, 0.1
-FP32_PEAK_NOTE = "148 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"
-FP64_PEAK_TFLOPS = 1.25  # B300 nominal FP64 (non-tensor) rate
 
 
 def parse():
@@ -53,10 +58,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_CELLS_1D, help="cells per direction")
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed FP64 steps (default: --steps)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    ap.add_argument("--boxes", type=int, default=24, help="9^3 boxes the oracle steps for the CPU baseline and the "
+                                                        "error against the oracle")
+    ap.add_argument("--ref-n", type=int, default=16, help="grid of the reference arm's oracle steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stage64", action="store_true", help="skip the FP32-flux / FP64-stage leg")
     ap.add_argument("--adjoint-n", type=int, default=64, help="cells per direction of the adjoint leg (0: skip)")
-    ap.add_argument("--adjoint-steps", type=int, default=4, help="checkpointed steps of the adjoint leg")
+    ap.add_argument("--adjoint-steps", type=int, default=100, help="checkpointed steps of the adjoint leg")
     return ap.parse_args()
 
 
@@ -122,58 +130,104 @@ def workload_config(n, dt):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(n, seconds, reps=1, Q=None):
-    """Time the oracle's residual on a bounded sample of cells of the workload.
-
-    Returns (DOF-stage-updates/s per repetition, threads, sample description)."""
+def sample_cells(n, count):
+    """Cells (i, j, k) of the n^3 grid whose 9^3 boxes the oracle steps: the corners and an interior
+    cell, then seeded random ones."""
     import numpy as np
 
+    rng = np.random.default_rng(5)
+    fixed = [(0, 0, 0), (n - 1, n - 1, n - 1), (131 % n, 7 % n, 200 % n)]
+    return fixed + [tuple(int(x) for x in rng.integers(0, n, 3)) for _ in range(max(0, count - len(fixed)))]
+
+
+def box_of(Q0, n, cell):
+    """The periodic 9^3 box of the n^3 state around `cell` (device tensor in, numpy out) and its lower corner.
+
+    After 2 S2O4 steps (4 stages) a cell depends only on the cells within 4 face-neighbour hops, so
+    the oracle stepping the box reproduces the full-grid result at its centre exactly."""
+    import torch
+
+    i, j, k = cell
+    ix, iy, iz = (torch.tensor([(c + d) % n for d in range(-4, 5)], device=Q0.device) for c in (i, j, k))
+    sub = Q0.index_select(2, iz).index_select(3, iy).index_select(4, ix).cpu().numpy()
+    h = 2 * math.pi / n
+    lo = tuple(-math.pi + (c - 4) * h for c in (i, j, k))
+    return sub, lo
+
+
+def oracle_boxes(boxes, n, dt, nsteps=2):
+    """The oracle's nsteps S2O4 steps of each 9^3 box; returns (centre coefficients [cells][5][10], seconds,
+    threads)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    h = 2 * math.pi / n
+    out = []
+    t0 = time.perf_counter()
+    for sub, lo in boxes:
+        pb = oracle.Problem(order=ORDER, nq=NQ, n=(9, 9, 9), lo=lo, hi=tuple(x + 9 * h for x in lo), mu=MU, Pr=PR,
+                            gamma=GAMMA)
+        out.append(oracle.step(pb, sub, dt, nsteps)[:, :, 4, 4, 4])
+    el = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return np.array(out), el, threads
+
+
+def oracle_config1():
+    """BASELINE configuration 1 run in full by the oracle: 3D density advection, 8^3 P1, n_q = 2,
+    tau = 0.01 dt, CFL 0.1, S2O4 to t = 0.1.  Returns (DOF-stage-updates/s, seconds, steps)."""
     import oracle
     from paper_2202_13821_b300 import inputs
 
     oracle.build()
-    if Q is None:
-        Q = inputs.tgv_state(n, ORDER, device="cpu").numpy()
-    dt = inputs.tgv_dt(n, ORDER)
-    pb = oracle.Problem(order=ORDER, nq=NQ, n=(n, n, n), lo=(-math.pi,) * 3, hi=(math.pi,) * 3, mu=MU, Pr=PR,
-                        gamma=GAMMA)
-    rng = np.random.default_rng(0)
-    # calibrate on 64 cells, then size the sample to the time budget
-    cells = rng.integers(0, n ** 3, 64)
+    T = 0.1
+    dt = inputs.advection_dt(8, T=T)
+    ns = round(T / dt)
+    pb = oracle.Problem(order=1, nq=2, n=(8, 8, 8), lo=(0.0,) * 3, hi=(2.0,) * 3, tau_eps=0.01)
+    Q = oracle.project(pb, oracle.IC_ADVECTION, (0.2, 0.0))
     t0 = time.perf_counter()
-    oracle.residual_cells(pb, Q, dt, cells)
-    per_cell = (time.perf_counter() - t0) / len(cells)
-    ncells = int(max(64, min(n ** 3, seconds / max(per_cell, 1e-9) / reps)))
-    cells = rng.integers(0, n ** 3, ncells)
-    rates = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        oracle.residual_cells(pb, Q, dt, cells)
-        el = time.perf_counter() - t0
-        rates.append(ncells * 5 * 10 / el)  # one stage of 50 DOFs per cell residual
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = (f"oracle residual (FP64, L and L_t, each cell evaluating its own six faces) of {ncells} random cells "
-              f"of the {n}^3 workload, {reps} repetition(s); DOF-stage-updates/s = cells x 50 / time")
-    return rates, threads, sample
+    oracle.step(pb, Q, dt, ns)
+    el = time.perf_counter() - t0
+    return 8 ** 3 * 5 * 4 * 2 * ns / el, el, ns
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the method written plainly from the paper), timed on the host
+    cores.  Each step is one whole S2O4 step of the oracle on a periodic Taylor-Green grid of
+    --ref-n^3 cells (P2, n_q = 3, the workload's physics and dt rule at a size the CPU steps in a few
+    seconds; the per-DOF cost does not depend on the grid size)."""
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
-    n = args.n
+    import oracle
     from paper_2202_13821_b300 import inputs
 
-    dt = inputs.tgv_dt(n, ORDER)
-    budget = max(4.0, min(15.0, 100.0 / max(1, args.steps + args.warmup)))
-    rates, threads, sample = oracle_sample(n, budget, reps=args.steps + args.warmup)
-    timed = rates[args.warmup:] or rates
-    value = statistics.mean(timed)  # rank 0 alone runs the CPU oracle
-    ms_per_step = 5 * 10 * n ** 3 * 2 / value * 1e3
+    oracle.build()
+    m = args.ref_n
+    dt = inputs.tgv_dt(m, ORDER)
+    pb = oracle.Problem(order=ORDER, nq=NQ, n=(m, m, m), lo=(-math.pi,) * 3, hi=(math.pi,) * 3, mu=MU, Pr=PR,
+                        gamma=GAMMA)
+    Q = inputs.tgv_state(m, ORDER, device="cpu").numpy()
+    times = []
+    for _ in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        Q = oracle.step(pb, Q, dt, 1)
+        times.append(time.perf_counter() - t0)
+    timed = times[args.warmup:] or times
+    sec = statistics.mean(timed)
+    value = 5 * 10 * m ** 3 * 2 / sec
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"oracle (FP64, each cell evaluating its own six faces), whole S2O4 steps of the Taylor-Green "
+              f"vortex on a periodic {m}^3 grid, P2, n_q = 3, dt from CFL 0.15 ({dt:.3e}); "
+              f"DOF-stage-updates/s = {m}^3 x 50 x 2 / step time")
+    cfg = workload_config(args.n, inputs.tgv_dt(args.n, ORDER))
+    cfg["reference_sample"] = {"cells": m ** 3, "dt": dt}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(n, dt),
+        "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -262,43 +316,56 @@ def profiled_traffic(kernel: str, n: int):
     return None, None
 
 
-def measured_peaks():
-    try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        return {}
-
-
-def run_leg(torch, api, precision, Q0, dt, warmup, steps, barrier, clock=None):
-    s = api.Solver((Q0.shape[4], Q0.shape[3], Q0.shape[2]), (-math.pi,) * 3, (math.pi,) * 3, order=ORDER,
+def run_leg(torch, api, precision, Q0, dt, warmup, steps, barrier, clock=None, prof_steps=3, cells=()):
+    """One precision on the workload: the states after 2 steps at the sampled cells (for the error against
+    the oracle), `warmup` untimed steps, `steps` timed steps of the production path (one dghgks_steps call,
+    CUDA-graph replay, no per-launch events), then a separate profiled pass of `prof_steps` steps on a copy
+    (each launch bracketed by CUDA events) for the per-kernel times of the roofline."""
+    n = Q0.shape[4]
+    s = api.Solver((n, Q0.shape[3], Q0.shape[2]), (-math.pi,) * 3, (math.pi,) * 3, order=ORDER,
                    gamma=GAMMA, mu=MU, Pr=PR, n_q=NQ, precision=precision)
+    centres = None
+    if cells:
+        Q2 = Q0.clone()
+        s.steps(Q2, dt, 2)
+        s.status()
+        centres = torch.stack([Q2[:, :, k, j, i] for (i, j, k) in cells]).cpu().numpy()
+        del Q2
     Q = Q0.clone()
     ek = [s.kinetic_energy(Q)]
     for _ in range(warmup):
-        s.step(Q, dt)
+        s.steps(Q, dt, 1)
         ek.append(s.kinetic_energy(Q))
     s.status()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.steps(Q.clone(), dt, 2)  # capture both step graphs of this dt outside the timed region
     torch.cuda.synchronize()
     barrier()
     launches0 = s.launches
-    s.profile(True)
     if clock is not None:
         clock.start()
     e0.record(stream)
-    s.steps(Q, dt, steps)  # FP32-mixed: the state rounded to FP32 carries over between the steps
+    s.steps(Q, dt, steps)  # FP32 contexts: the state rounded to FP32 carries over between the steps
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clock.stop() if clock is not None else None
     barrier()
     ms = e0.elapsed_time(e1)
-    prof = s.profile_read()
-    s.profile(False)
     launches = s.launches - launches0
     s.status()
     ek.append(s.kinetic_energy(Q))
-    return {"solver": s, "Q": Q, "ms": ms, "prof": prof, "launches": launches, "ek": ek, "clocks": clocks}
+    prof = None
+    if prof_steps > 0:
+        Qp = Q.clone()
+        s.profile(True)
+        s.steps(Qp, dt, prof_steps)
+        prof = s.profile_read()
+        s.profile(False)
+        s.status()
+        del Qp
+    return {"solver": s, "Q": Q, "ms": ms, "prof": prof, "launches": launches, "ek": ek, "clocks": clocks,
+            "centres": centres}
 
 
 def algorithmic_bytes(kernel, precision):
@@ -308,22 +375,40 @@ def algorithmic_bytes(kernel, precision):
     k_face stage 1 reads the state and writes the F and F_t moments; stage 2 reads Q* (flux
     precision) and writes the F_t moments.  k_cell stage 1 reads the state and the moments of its
     faces and writes Q* and inc; stage 2 reads Q*, inc, the F_t moments and the FP64 state and
-    writes the state.  FP32-mixed steps read the state rounded to FP32 at stage 1, which stage 2
-    writes besides the FP64 state (the rounding kernel at the start of a call is not counted)."""
-    r = 4 if precision == 1 else 8
+    writes the state.  FP32 steps read the state rounded to FP32 at stage 1, which stage 2 writes
+    besides the FP64 state (the rounding kernel at the start of a call is not counted); with FP64
+    stage arithmetic (precision 2) inc is FP64 and stage 1 also reads the FP64 state for Q*."""
+    r = 4 if precision in (1, 2) else 8
+    e = 8 if precision in (0, 2) else 4
     coef, mom = 5 * 10, 10 * 6
-    state_in = coef * r  # FP32 copy (FP32-mixed) or the FP64 state
-    copy_out = coef * 4 if precision == 1 else 0
+    state_in = coef * r  # FP32 copy (FP32 contexts) or the FP64 state
+    copy_out = coef * 4 if precision in (1, 2) else 0
     if kernel == "k_face":
         s1 = state_in + mom * r
         s2 = coef * r + mom // 2 * r
     else:
-        s1 = state_in + 3 * mom * r + 2 * coef * r  # six faces, each shared by two cells
-        s2 = 2 * coef * r + 3 * (mom // 2) * r + 2 * coef * 8 + copy_out
+        s1 = state_in + 3 * mom * r + coef * r + coef * e + (coef * 8 if precision == 2 else 0)
+        s2 = coef * r + coef * e + 3 * (mom // 2) * r + 2 * coef * 8 + copy_out
     return (s1 + s2) / 2
 
 
-def roofline_entry(prof, precision, n, peaks, clocks):
+def charged_flops(point, rates):
+    """Work of one flux point in FP32 FMA-equivalent FLOP: the counted additions and multiplications, and
+    each division, reciprocal square root, exponential and erfc at its measured cost (the FMA FLOPs the
+    GPU issues in the time of one such operation, from dghgks_pipe_rates).  The counter records a
+    reciprocal square root as a square root and a division by it; on the GPU it is one instruction."""
+    c = {k: rates["ffma_flops"] / rates[k + "_ops"] for k in ("div", "rsqrt", "exp", "erfc")}
+    base = point["total_flops"] - point["div"]
+    extra = (point["div"] - point["sqrt"]) * c["div"] + point["sqrt"] * c["rsqrt"] + point["exp"] * c["exp"] + \
+        point["erfc"] * c["erfc"]
+    return base, extra, c
+
+
+def roofline_entry(prof, precision, n, rates, clocks):
+    """Roofline of the dominant kernel: algorithmic FLOPs per launch (value-numbered counts of the flux,
+    trace and projection arithmetic; FP32 contexts also charge the transcendentals at their measured
+    cost) over the kernel's mean CUDA-event launch time in the profiled pass, against the measured FMA
+    rate of this GPU (dghgks_pipe_rates)."""
     from paper_2202_13821_b300 import build
 
     oc = build.opcounts(ORDER, NQ, PR != 1.0)
@@ -333,46 +418,69 @@ def roofline_entry(prof, precision, n, peaks, clocks):
     cell_n = prof["cell_stage1"][1] + prof["cell_stage2"][1]
     pts = n ** 3 * NQ * NQ  # face points of one face launch (one normal direction)
     cpts = n ** 3 * NQ ** 3
-    # a step launches each kernel once per stage; the stage-2 launches need
-    # F_t only (the counts keep only the operations F_t depends on), so the
-    # per-launch figure is the mean of the two
-    face_flops = pts * (oc["face_point"]["total_flops"] + oc["face_point"]["total_flops_ft"]) // 2
-    cell_flops = cpts * (oc["cell_point"]["total_flops"] + oc["cell_point"]["total_flops_ft"]) // 2
-    kernels = {
-        "k_face": {"launches": face_n, "avg_ms": face_ms / max(face_n, 1), "flops_per_launch": face_flops},
-        "k_cell": {"launches": cell_n, "avg_ms": cell_ms / max(cell_n, 1), "flops_per_launch": cell_flops},
-    }
+    fp32 = precision in (1, 2)
+    kernels = {}
+    for name, npts, ms_, nl, key in (("k_face", pts, face_ms, face_n, "face_point"),
+                                     ("k_cell", cpts, cell_ms, cell_n, "cell_point")):
+        pt = oc[key]
+        # a step launches each kernel once per stage; the stage-2 launches need F_t only (the counts keep
+        # only the operations F_t depends on; the transcendentals are needed by both), so the per-launch
+        # figure is the mean of the two
+        counted = npts * (pt["total_flops"] + pt["total_flops_ft"]) / 2
+        charged = counted
+        if fp32:
+            base, extra, _ = charged_flops(pt, rates)
+            charged = counted - npts * pt["div"] + npts * extra
+        kernels[name] = {"launches": nl, "avg_ms": ms_ / max(nl, 1), "flops_per_launch": counted,
+                         "charged_flops_per_launch": charged}
     dom = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
     kd = kernels[dom]
-    achieved = kd["flops_per_launch"] / (kd["avg_ms"] * 1e-3) / 1e12
-    smax = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2032.0)
-    if precision == 1:
-        peak = 148 * 128 * 2 * smax * 1e6 / 1e12
-        peak_src = f"derived: {FP32_PEAK_NOTE} = {peak:.1f} TFLOP/s (FP32)"
+    achieved = kd["charged_flops_per_launch"] / (kd["avg_ms"] * 1e-3) / 1e12
+    achieved_counted = kd["flops_per_launch"] / (kd["avg_ms"] * 1e-3) / 1e12
+    sms = rates.get("sms", 148)
+    smax = (clocks or {}).get("sm_max_mhz") or 2032.0
+    if fp32:
+        peak = rates["ffma_flops"] / 1e12
+        derived = sms * 128 * 2 * smax * 1e6 / 1e12
+        peak_src = (f"measured: FP32 FMA loop (dghgks_pipe_rates, {int(sms)} SMs) = {peak:.1f} TFLOP/s; "
+                    f"derived {int(sms)} SMs x 128 lanes x 2 x {smax:.0f} MHz = {derived:.1f}")
+        charges = charged_flops(oc["face_point"], rates)[2]
     else:
-        peak = FP64_PEAK_TFLOPS
-        peak_src = "B300 FP64 1.25 TFLOP/s nominal (a DFMA loop measured 0.95 on a B300)"
+        peak = rates["dfma_flops"] / 1e12
+        derived = None
+        peak_src = f"measured: FP64 FMA loop (dghgks_pipe_rates) = {peak:.3f} TFLOP/s (B300 nominal 1.25)"
+        charges = None
     traffic, traffic_src = profiled_traffic(dom, n) if precision == 1 else (None, None)
-    return {
-        "bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+    entry = {
+        "bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
         "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_source": traffic_src,
         "traffic_algorithmic": n ** 3 * algorithmic_bytes(dom, precision),
-        "peak_source": peak_src,
+        "peak_source": peak_src, "peak_derived": derived,
+        "achieved_counted_only": round(achieved_counted, 3), "frac_counted_only": round(achieved_counted / peak, 4),
         "algorithmic_flops": "value-numbered op count per point x points per launch, mean of the two stages "
                              f"(face point {oc['face_point']['total_flops']} / {oc['face_point']['total_flops_ft']} "
                              f"F_t only; cell point {oc['cell_point']['total_flops']} / "
-                             f"{oc['cell_point']['total_flops_ft']} F_t only)",
+                             f"{oc['cell_point']['total_flops_ft']} F_t only)" +
+                             ("; achieved charges each div / rsqrt / exp / erfc at its measured cost in FMA FLOPs "
+                              "(charged_flops_per_launch), achieved_counted_only counts each as 1" if fp32 else ""),
+        "transcendental_charge_flops": ({k: round(v, 2) for k, v in charges.items()} if charges else None),
         "kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                     for k, v in kernels.items()},
     }
+    return entry
 
 
 def run_adjoint(torch, api, n, nsteps):
     """Gradient of the final E_k w.r.t. the initial state and mu over nsteps checkpointed FP64 steps
-    (Taylor-Green P2): time per forward and per adjoint step, checkpoint and device memory."""
+    (Taylor-Green P2): measured time per forward and per adjoint step, checkpoint bytes, peak device
+    memory of torch's allocator (the checkpoints and the adjoint state) and the device memory in use
+    after the forward pass (cudaMemGetInfo: also the library's own scratch)."""
     from paper_2202_13821_b300 import autograd, inputs
 
     dt = inputs.tgv_dt(n, ORDER)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    base_alloc = torch.cuda.memory_allocated()
     free0, _ = torch.cuda.mem_get_info()
     s = api.Solver((n,) * 3, (-math.pi,) * 3, (math.pi,) * 3, order=ORDER, gamma=GAMMA, mu=MU, Pr=PR, n_q=NQ,
                    precision=api.DGHGKS_FP64)
@@ -388,9 +496,11 @@ def run_adjoint(torch, api, n, nsteps):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     state = Q0.numel() * 8
+    fwd, adj = 1e3 * (t1 - t0) / nsteps, 1e3 * (t2 - t1) / nsteps
     out = {"workload": f"Taylor-Green {n}^3 P2 FP64, {nsteps} checkpointed S2O4 steps, dE_k/d(Q0, mu)",
-           "forward_ms_per_step": 1e3 * (t1 - t0) / nsteps, "adjoint_ms_per_step": 1e3 * (t2 - t1) / nsteps,
-           "checkpoint_bytes_per_step": state, "checkpoint_bytes_100_steps": 100 * state,
+           "steps": nsteps, "forward_ms_per_step": fwd, "adjoint_ms_per_step": adj, "adjoint_over_forward": adj / fwd,
+           "checkpoint_bytes_per_step": state, "checkpoint_bytes": nsteps * state,
+           "torch_peak_bytes": torch.cuda.max_memory_allocated() - base_alloc,
            "device_bytes_after_forward": free0 - free1, "dJ_dmu": float(mu.grad.item()),
            "grad_norm": float(Q0.grad.norm().item())}
     s.close()
@@ -399,7 +509,17 @@ def run_adjoint(torch, api, n, nsteps):
     return out
 
 
+def pipe_rates(api, local):
+    """Measured FMA and transcendental rates of this GPU, with the SM clock sampled meanwhile."""
+    clock = ClockSampler(local)
+    clock.start()
+    r = api.dghgks_pipe_rates()
+    r["clocks"] = clock.stop()
+    return r
+
+
 def run_ours(args):
+    import numpy as np
     import torch
 
     rank, world, local = dist_info()
@@ -417,82 +537,128 @@ def run_ours(args):
     flux_step = 2 * (3 * n ** 3 * NQ ** 2 + n ** 3 * NQ ** 3)
     Q0 = inputs.tgv_state(n, ORDER, device="cuda")
     torch.cuda.synchronize()
-    peaks = measured_peaks()
+    rates = pipe_rates(api, local)
+    do_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    cells = sample_cells(n, args.boxes) if do_cpu else ()
 
     # --- FP32-mixed (headline) ---
-    m32 = run_leg(torch, api, api.DGHGKS_FP32_MIXED, Q0, dt, args.warmup, args.steps, barrier, ClockSampler(local))
+    m32 = run_leg(torch, api, api.DGHGKS_FP32_MIXED, Q0, dt, args.warmup, args.steps, barrier,
+                  ClockSampler(local), cells=cells)
     clocks = m32["clocks"]
     ms32 = max_over_ranks(m32["ms"]) / args.steps
     value = ranks.job_rate(dof_step, ms32 * 1e-3)
     m32["solver"].close()  # free its scratch; the final state Q stays
 
+    # --- FP32 flux with FP64 stage arithmetic ---
+    ms_s = m_s = None
+    if not args.no_stage64:
+        m_s = run_leg(torch, api, api.DGHGKS_FP32_STAGE64, Q0, dt, args.warmup, args.steps, barrier, cells=cells)
+        ms_s = max_over_ranks(m_s["ms"]) / args.steps
+        m_s["solver"].close()
+
     # --- FP64 on the same state ---
     k64 = args.fp64_steps if args.fp64_steps is not None else args.steps
-    m64 = run_leg(torch, api, api.DGHGKS_FP64, Q0, dt, args.warmup, k64, barrier)
+    m64 = run_leg(torch, api, api.DGHGKS_FP64, Q0, dt, args.warmup, k64, barrier, prof_steps=1, cells=cells)
     ms64 = max_over_ranks(m64["ms"]) / k64
     value64 = ranks.job_rate(dof_step, ms64 * 1e-3)
 
-    # --- error of FP32-mixed against FP64 after the same steps (when the step counts agree) ---
+    # --- errors of the FP32 paths against FP64 after the same steps (when the step counts agree) ---
     s64 = m64["solver"]
     err = {"steps_compared": args.warmup + args.steps if k64 == args.steps else None}
-    if k64 == args.steps:
-        l2 = s64.l2_diff(m32["Q"], m64["Q"], 0)
-        l2E = s64.l2_diff(m32["Q"], m64["Q"], 4)
-        l2_change = s64.l2_diff(m64["Q"], Q0, 0)
-        err.update({"l2_rho_fp32_vs_fp64": l2, "l2_rhoE_fp32_vs_fp64": l2E,
-                    "l2_rho_change_over_run": l2_change})
+    l2_change = s64.l2_diff(m64["Q"], Q0, 0) if k64 == args.steps else None
+    for tag, m in (("fp32", m32), ("fp32_stage64", m_s)):
+        if m is None:
+            continue
+        e = {}
+        if k64 == args.steps:
+            e["l2_rho_vs_fp64"] = s64.l2_diff(m["Q"], m64["Q"], 0)
+            e["l2_rhoE_vs_fp64"] = s64.l2_diff(m["Q"], m64["Q"], 4)
+            e["l2_rho_change_over_run"] = l2_change
+            e["ratio_rho"] = e["l2_rho_vs_fp64"] / l2_change
+        dek = [abs(a - b) / abs(b) for a, b in zip(m["ek"], m64["ek"])]
+        e["ek_rel_diff_max"] = max(dek)
+        e["ek_decay_rel_diff"] = (abs((m["ek"][-1] - m["ek"][0]) - (m64["ek"][-1] - m64["ek"][0])) /
+                                  abs(m64["ek"][-1] - m64["ek"][0])
+                                  if k64 == args.steps and m64["ek"][-1] != m64["ek"][0] else None)
+        err[tag] = e
+    err["ek_history_fp64"] = m64["ek"]
     s64.close()
     m64["solver"] = None
-    ek32, ek64 = m32["ek"], m64["ek"]
-    dek = [abs(a - b) / abs(b) for a, b in zip(ek32, ek64)]
-    err["ek_rel_diff_max"] = max(dek)
-    err["ek_history_fp64"] = ek64
-    err["ek_decay_rel_diff"] = (abs((ek32[-1] - ek32[0]) - (ek64[-1] - ek64[0])) / abs(ek64[-1] - ek64[0])
-                                if k64 == args.steps and ek64[-1] != ek64[0] else None)
 
-    roof = roofline_entry(m32["prof"], 1, n, peaks, clocks)
-    roof64 = roofline_entry(m64["prof"], 0, n, peaks, None)
+    roof = roofline_entry(m32["prof"], 1, n, rates, clocks)
+    roof64 = roofline_entry(m64["prof"], 0, n, rates, None)
+    roof_s = roofline_entry(m_s["prof"], 2, n, rates, None) if m_s is not None else None
 
     # --- end to end through the C ABI with host buffers (FP32-mixed) ---
-    e2e = None
-    if True:  # every rank measures its own replica end to end
-        host = torch.empty(Q0.shape, dtype=torch.float64, pin_memory=True)
-        host.copy_(Q0)
-        Qh = host.numpy()
-        s_e2e = api.Solver((n, n, n), (-math.pi,) * 3, (math.pi,) * 3, order=ORDER, gamma=GAMMA, mu=MU, Pr=PR,
-                           n_q=NQ, precision=api.DGHGKS_FP32_MIXED)
-        s_e2e.run_host(Qh, dt, 1)  # allocates the device state, warms up
-        host.copy_(Q0)
-        barrier()
-        t0 = time.perf_counter()
-        ek_e2e = s_e2e.run_host(Qh, dt, args.steps)
-        el = max_over_ranks(time.perf_counter() - t0)
-        state_bytes = Q0.numel() * 8
-        e2e = {"value": ranks.job_rate(dof_step * args.steps, el), "unit": UNIT,
-               "h2d_bytes_per_step": state_bytes / args.steps,
-               "d2h_bytes_per_step": (state_bytes + 8 * args.steps) / args.steps,
-               "api": "dghgks_run_host (H2D of the state, K steps with E_k read back after each, D2H of the state)",
-               "ek_last": float(ek_e2e[-1])}
-        s_e2e.close()
-        del host
+    host = torch.empty(Q0.shape, dtype=torch.float64, pin_memory=True)
+    host.copy_(Q0)
+    Qh = host.numpy()
+    s_e2e = api.Solver((n, n, n), (-math.pi,) * 3, (math.pi,) * 3, order=ORDER, gamma=GAMMA, mu=MU, Pr=PR,
+                       n_q=NQ, precision=api.DGHGKS_FP32_MIXED)
+    s_e2e.run_host(Qh, dt, 1)  # allocates the device state, warms up
+    host.copy_(Q0)
+    barrier()
+    t0 = time.perf_counter()
+    ek_e2e = s_e2e.run_host(Qh, dt, args.steps)
+    el = max_over_ranks(time.perf_counter() - t0)
+    state_bytes = Q0.numel() * 8
+    e2e = {"value": ranks.job_rate(dof_step * args.steps, el), "unit": UNIT,
+           "h2d_bytes_per_step": state_bytes / args.steps,
+           "d2h_bytes_per_step": (state_bytes + 8 * args.steps) / args.steps,
+           "api": "dghgks_run_host (H2D of the state, K steps with E_k read back after each, D2H of the state)",
+           "ek_last": float(ek_e2e[-1])}
+    s_e2e.close()
+    del host
 
     adj = run_adjoint(torch, api, args.adjoint_n, args.adjoint_steps) if args.adjoint_n > 0 else None
 
+    # --- CPU baseline: the oracle on 9^3 boxes of the workload (2 steps each), and BASELINE config 1 ---
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rates, threads, sample = oracle_sample(n, args.cpu_seconds, Q=Q0.cpu().numpy())
-        cpu = {"value": rates[0], "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+    if do_cpu:
+        boxes = [box_of(Q0, n, c) for c in cells]
+        want, sec, threads = oracle_boxes(boxes, n, dt)
+        cfg1_rate, cfg1_s, cfg1_steps = oracle_config1()
+        nb = len(cells)
+        cpu = {"value": nb * 9 ** 3 * 50 * 2 * 2 / sec, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"oracle (FP64) stepping {nb} periodic 9^3 boxes cut from the {n}^3 workload around sampled "
+                         f"cells, 2 S2O4 steps each, {sec:.1f} s; DOF-stage-updates/s = boxes x 729 x 50 x 2 stages x "
+                         f"2 steps / time",
+               "config1_full_run": {"value": cfg1_rate, "seconds": cfg1_s, "steps": cfg1_steps,
+                                    "workload": "3D density advection 8^3 P1, n_q = 2, S2O4 to t = 0.1"}}
+        # error of each GPU path against the oracle at the box centres after 2 steps (the 9^3 box holds every
+        # cell a centre depends on after 4 stages, so the oracle's centre values are those of the full grid)
+        Q0c = torch.stack([Q0[:, :, k, j, i] for (i, j, k) in cells]).cpu().numpy()
+        w = np.array([(2 * a + 1) * (2 * b + 1) * (2 * c + 1) for (a, b, c) in
+                      ((0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2), (1, 1, 0),
+                       (1, 0, 1), (0, 1, 1))], dtype=float)
+        rms = lambda d: float(np.sqrt(np.mean(np.sum(d[:, 0, :] ** 2 / w, axis=1))))  # density, cell-mean L2
+        vo = {"cells": nb, "steps": 2, "rms_rho_change": rms(want - Q0c)}
+        for tag, m in (("fp64", m64), ("fp32", m32), ("fp32_stage64", m_s)):
+            if m is None or m["centres"] is None:
+                continue
+            d = m["centres"] - want
+            vo[tag] = {"rms_rho_err": rms(d), "ratio_rho": rms(d) / vo["rms_rho_change"],
+                       "max_abs_err_per_var": np.abs(d).max(axis=(0, 2)).tolist()}
+        err["vs_oracle"] = vo
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32-mixed (f32 flux/quadrature, f64 stage + reductions)",
+            "vs_baseline": None, "dtype": "f32-mixed (f32 flux/quadrature/projection/stage increments, f64 state "
+                                          "accumulation + reductions)",
             "data": "synthetic", "config": workload_config(n, dt),
+            "timing": "one dghgks_steps call of K steps (CUDA-graph replay), CUDA events on the stream; per-kernel "
+                      "times from a separate profiled pass",
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "steps": k64, "dtype": "f64",
                      "roofline": roof64},
+            "fp32_stage64": (None if m_s is None else
+                             {"value": ranks.job_rate(dof_step, ms_s * 1e-3), "unit": UNIT, "ms_per_step": ms_s,
+                              "dtype": "f32 flux/quadrature/projection, f64 assembly + M^-1 + S2O4 combination",
+                              "roofline": roof_s}),
             "error": err, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": m32["launches"],
+            "pipe_rates": rates,
             "adjoint": adj,
             # companion metric: gas-kinetic flux evaluations (face and cell Gauss points, both stages;
             # one face point counts once, with both of its time integrals)

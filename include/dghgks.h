@@ -53,7 +53,16 @@ extern "C" {
 #define DGHGKS_ESCRATCH (-6) /* problem too large for dghgks_residual_static's fixed scratch */
 
 #define DGHGKS_FP64 0       /* flux and quadrature arithmetic in FP64 */
-#define DGHGKS_FP32_MIXED 1 /* flux/quadrature in FP32; stage arithmetic and reductions FP64 */
+/* FP32-mixed: flux, quadrature, projection sums, the face-moment assembly,
+ * M^-1 and the stage increments in FP32; the stored state, its update and
+ * the reductions in FP64 */
+#define DGHGKS_FP32_MIXED 1
+/* FP32 flux, quadrature and projection sums (as DGHGKS_FP32_MIXED); the
+ * assembly of a cell's volume and face contributions, M^-1 and the S2O4 stage
+ * combination (Q*, the stage increment, the state update) in FP64, with the
+ * stage increment stored in FP64 and Q* stored rounded to FP32 (its only
+ * reader is the FP32 flux arithmetic of stage 2) */
+#define DGHGKS_FP32_STAGE64 2
 
 typedef struct dghgks_ctx dghgks_ctx;
 
@@ -76,7 +85,7 @@ typedef struct {
 } dghgks_mesh;
 
 /* n_q: Gauss points per direction (faces n_q^2, cells n_q^3); 0 = order+1.
- * precision: DGHGKS_FP64 or DGHGKS_FP32_MIXED.
+ * precision: DGHGKS_FP64, DGHGKS_FP32_MIXED or DGHGKS_FP32_STAGE64.
  * tau_eps: tau = mu/p + tau_eps*dt (0 = the paper's tau = mu/p). */
 typedef struct {
   int n_q;
@@ -91,7 +100,8 @@ typedef struct {
  * to the energy flux, which the paper does not define).  opts may be NULL
  * (n_q = order+1, FP64, tau_eps = 0).  Uses the current CUDA device.
  * Allocates the scratch: 2 stage buffers with the state's values in the flux
- * precision (3 on an FP32-mixed context: also the FP32 state copy) plus the
+ * precision (Q* and the stage increment; the increment in FP64 with
+ * DGHGKS_FP32_STAGE64), on FP32 contexts also the FP32 state copy, plus the
  * face moments (3 * 10 * (k+1)(k+2)/2 values per cell in the flux precision). */
 int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, double Pr, const dghgks_opts* opts,
                 dghgks_ctx** out);
@@ -117,8 +127,9 @@ int dghgks_residual(dghgks_ctx* ctx, const double* Q, double dt, double* L, doub
 /* One S2O4 step (Sec. 3, Eq. two-stage), in place on the device state Q:
  *   Q* = Q + dt/2 L(Q) + dt^2/8 L_t(Q)
  *   Q <- Q + dt L(Q) + dt^2/6 (L_t(Q) + 2 L_t(Q*)).
- * On an FP32-mixed context the stage-1 kernels read Q rounded to FP32 (one
- * extra elementwise launch rounds it into a library buffer).
+ * On an FP32 context (DGHGKS_FP32_MIXED or DGHGKS_FP32_STAGE64) the stage-1
+ * kernels read Q rounded to FP32 (one extra elementwise launch rounds it into
+ * a library buffer).
  * Asynchronous; consecutive calls on one context must share a stream. */
 int dghgks_step(dghgks_ctx* ctx, double* Q, double dt, void* stream);
 
@@ -126,7 +137,7 @@ int dghgks_step(dghgks_ctx* ctx, double* Q, double dt, void* stream);
  * of one step (8 kernel launches) on `stream`.  The graphs are captured on a
  * private stream at the first call and re-captured when Q, dt or the
  * viscosity (dghgks_set_mu) changes (the executable graph is updated in
- * place when possible).  On an FP32-mixed context the stage-1 kernels read the
+ * place when possible).  On an FP32 context the stage-1 kernels read the
  * state rounded to FP32 in a library buffer: the first step of a call rounds Q
  * into it, and every step's state update writes it for the next step (a
  * second graph); Q may therefore change between calls but not during one.
@@ -226,7 +237,11 @@ int64_t dghgks_launch_count(const dghgks_ctx* ctx);
  * embedded loops that forbid allocation after initialisation, and code that
  * must not trigger the device-wide synchronisation of cudaFree.
  * Arguments are those of dghgks_init plus those of dghgks_residual; the caller
- * passes Q, L, Lt (device, state layout, distinct buffers).
+ * passes Q, L, Lt (device, state layout, distinct buffers).  Supported: uniform
+ * periodic meshes (nodes all NULL), order 1 with n_q = 2 and order 2 with
+ * n_q = 2 or 3, precision DGHGKS_FP64 or DGHGKS_FP32_MIXED.  A rectilinear mesh
+ * (any nodes[d] != NULL), order 3 or another n_q return DGHGKS_EUNSUP, and
+ * DGHGKS_FP32_STAGE64 returns DGHGKS_EARG, all before any GPU work.
  * Scratch: the face moments live in one file-scope __device__ array of
  * DGHGKS_STATIC_SCRATCH_BYTES (16 MiB), which every GPU that loads the library
  * holds until the process exits; problems needing more
@@ -243,6 +258,18 @@ int64_t dghgks_launch_count(const dghgks_ctx* ctx);
 #define DGHGKS_STATIC_SCRATCH_BYTES (16u << 20)
 int dghgks_residual_static(const dghgks_mesh* mesh, int order, double gamma, double mu, double Pr,
                            const dghgks_opts* opts, const double* Q, double dt, double* L, double* Lt, void* stream);
+
+/* Measured arithmetic throughput of the current GPU, for the roofline of the
+ * (ALU-bound) residual kernels; the paper has no counterpart.  out[0..6]
+ * (host memory, n_out >= DGHGKS_NRATES): FP32 FMA FLOP/s (2 FLOP per FFMA),
+ * FP64 FMA FLOP/s, then operations/s of the FP32 flux's approximate division,
+ * reciprocal square root and exponential and of erfcf (each loop iteration is
+ * the operation plus one FP32 add), and the SM count.  Each rate is the best
+ * of three launches of about 10-20 ms filling every SM.  Allocates and frees
+ * a small device buffer; synchronises the device; returns 0, DGHGKS_EARG,
+ * DGHGKS_ENOMEM or DGHGKS_ECUDA. */
+#define DGHGKS_NRATES 7
+int dghgks_pipe_rates(double* out, int n_out);
 
 /* Gauss-Legendre rule used on the device: nodes x[n] ascending on [-1,1],
  * weights w[n] normalised to sum 1 (n = 1..5).  Host-only, no GPU needed. */

@@ -20,6 +20,7 @@ _SO = os.path.join(_HERE, "libdghgks.so")
 
 DGHGKS_FP64 = 0
 DGHGKS_FP32_MIXED = 1
+DGHGKS_FP32_STAGE64 = 2  # FP32 flux; FP64 assembly, M^-1 and S2O4 stage combination
 ERRORS = {-1: "bad argument", -2: "unsupported", -3: "CUDA error", -4: "non-physical state", -5: "out of memory",
           -6: "problem exceeds the fixed scratch of dghgks_residual_static"}
 
@@ -70,6 +71,7 @@ _SIGS = {
     "dghgks_kinetic_energy_vjp": (_I, [_VP, _VP, _D, _VP, _VP]),
     "dghgks_profile": (_I, [_VP, _I]),
     "dghgks_profile_read": (_I, [_VP, _DP, ctypes.POINTER(ctypes.c_int64)]),
+    "dghgks_pipe_rates": (_I, [_DP, _I]),
 }
 
 NKINDS = 7
@@ -152,6 +154,17 @@ def dghgks_residual_static(n, lo, hi, order: int, gamma: float, mu: float, Pr: f
                                        _ptr(L), _ptr(Lt), _stream(stream))
     if rc != 0:
         raise DghgksError(rc, "dghgks_residual_static")
+
+
+def dghgks_pipe_rates() -> dict:
+    """Measured FP32/FP64 FMA FLOP/s, operations/s of the FP32 flux's division, rsqrt, exp and erfc,
+    and the SM count of the current device (see include/dghgks.h)."""
+    out = np.zeros(7)
+    rc = load().dghgks_pipe_rates(out.ctypes.data_as(_DP), 7)
+    if rc != 0:
+        raise DghgksError(rc, "dghgks_pipe_rates")
+    keys = ("ffma_flops", "dfma_flops", "div_ops", "rsqrt_ops", "exp_ops", "erfc_ops", "sms")
+    return dict(zip(keys, out.tolist()))
 
 
 def dghgks_destroy(ctx):

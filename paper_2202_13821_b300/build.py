@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SO = os.path.join(HERE, "libdghgks.so")
 SOURCES = [os.path.join(HERE, "csrc", "dghgks_api.cu"), os.path.join(HERE, "csrc", "dghgks_static.cu"),
-           os.path.join(HERE, "csrc", "dghgks_adjoint.cu")]
+           os.path.join(HERE, "csrc", "dghgks_adjoint.cu"), os.path.join(HERE, "csrc", "dghgks_peaks.cu")]
 # extra device-compiler options per source (see the header of dghgks_adjoint.cu)
 EXTRA = {"dghgks_adjoint.cu": ["-Xptxas", "-O1"]}
 DEPS = [os.path.abspath(__file__)] + SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc")) if f.endswith((".cu", ".cuh"))] + [

@@ -8,12 +8,14 @@
 //     staging the two cells of each face (coalesced loads), it contracts
 //     their modal coefficients along the normal, so each side's trace is a
 //     2-D polynomial in the tangential coordinates (value and normal
-//     derivative).  One warp per Gauss point, lanes over faces: each thread
-//     evaluates Q_h and grad Q_h on both sides of its point, computes F_b and
-//     d_t F_b there (Eq. flux, local frame with the normal first), and the CTA
-//     projects w |Gamma| F onto the NT tangential Legendre products of the
-//     face in shared memory.  Only those face moments G reach HBM (10 x NT
-//     values per face); point values never do.
+//     derivative).  Lanes run over faces; in FP32 a thread takes the n_q
+//     Gauss points of one row of its face in turn (n_q warps per CTA), in
+//     FP64 one warp per Gauss point.  At each of its points a thread
+//     evaluates Q_h and grad Q_h on both sides, computes F_b and d_t F_b there
+//     (Eq. flux, local frame with the normal first), and the CTA projects
+//     w |Gamma| F onto the NT tangential Legendre products of the face in
+//     shared memory.  Only those face moments G reach HBM (10 x NT values per
+//     face); point values never do.
 //
 //   k_cell<MODE>: a group of lanes owns one cell, one lane per Gauss point
 //     (a warp per cell at n_q = 3, four cells per warp at n_q = 2).  Each lane
@@ -27,10 +29,14 @@
 //       MODE 0: write L = M^-1 R and L_t = M^-1 R_t
 //       MODE 1: Q* = Q^n + dt/2 L + dt^2/8 L_t, inc = dt L + dt^2/6 L_t
 //       MODE 2: Q^{n+1} = Q^n + inc + dt^2/3 L_t(Q*)
-//     Q* and inc are stored in the flux precision (the stage-2 kernels read
-//     Q* in that precision anyway); the accumulation into the stored FP64
-//     state is FP64.  On B300 an FP64 instruction costs ~64 FP32 ones, so the
-//     FP32-mixed path keeps FP64 to this single add per coefficient and step.
+//     The epilogue runs in the precision E: E = R (FP64, and the FP32-mixed
+//     path) stores Q* and inc in the flux precision, and the accumulation into
+//     the stored FP64 state is the one FP64 operation (on B300 an FP64
+//     instruction costs ~64 FP32 ones).  E = double with R = float (the
+//     FP32-flux / FP64-stage path): the volume sums leave the butterflies in
+//     FP32, and the assembly with the face moments, M^-1, Q* and inc are FP64
+//     (Q* formed from the FP64 state and stored rounded to R, its precision
+//     as an input of the stage-2 flux kernels; inc stored in FP64).
 //
 // Each face is computed exactly once and written by exactly one CTA, and
 // every residual coefficient is summed in a fixed order: results are
@@ -417,7 +423,7 @@ struct CellLayout {
   static_assert(NP <= 64, "k_cell handles up to 4^3 points per cell");
 };
 
-template <class R, int ORDER, int NQ, class Tin = R>
+template <class R, int ORDER, int NQ, class Tin = R, class E = R>
 struct CellSmem {
   using LY = CellLayout<ORDER, NQ>;
   static constexpr int NM = LY::NM, NC = 5 * NM, CB = LY::CB;
@@ -430,8 +436,8 @@ struct CellSmem {
   static constexpr size_t red = LY::GW == 1 ? 0 : sizeof(R) * CB * LY::GW * 2 * LY::NOP;
   // GW = 1: the outputs of a tile (two kinds, NC x CB), double-buffered, so
   // that they leave as rows of CB consecutive cells
-  static constexpr size_t out = LY::GW == 1 ? sizeof(R) * 2 * 2 * NC * CB : 0;
-  static constexpr size_t tabs = sizeof(R) * NM + sizeof(int) * 6 * NM;
+  static constexpr size_t out = LY::GW == 1 ? sizeof(E) * 2 * 2 * NC * CB : 0;
+  static constexpr size_t tabs = sizeof(E) * NM + sizeof(int) * 6 * NM;
   static constexpr size_t cvt_off = raw, red_off = raw + cvt, out_off = raw + cvt + red, tab_off = out_off + out;
   static constexpr size_t bytes = raw + cvt + red + out + tabs;
 };
@@ -481,19 +487,20 @@ __device__ __forceinline__ void cp_async_zfill(T* smem, const T* gmem, bool vali
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Buffers of the cell-kernel epilogue.
+// Buffers of the cell-kernel epilogue (E: its precision, see the header).
 //   MODE 0: L, Lt (FP64, caller's)
-//   MODE 1: Qs = Q* and inc = dt L + dt^2/6 L_t, both in the flux precision R
-//           (the stage-2 kernels read Q* in R; nothing is lost)
+//   MODE 1: Qs = Q* in the flux precision R (the stage-2 kernels read Q* in R)
+//           and inc = dt L + dt^2/6 L_t in E; with E = double, Q* is formed
+//           from the FP64 state Qn
 //   MODE 2: Qn (FP64 state, updated in place) += inc + dt^2/3 L_t(Q*); when Qf
 //           is not null, also Qf = the updated state rounded to R (the next
 //           step's stage-1 kernels read it instead of converting Qn)
-template <class R>
+template <class R, class E = R>
 struct StageIO {
   double* L;
   double* Lt;
   R* Qs;
-  R* inc;
+  E* inc;
   double* Qn;
   R* Qf;
 };
@@ -512,17 +519,18 @@ template <class R, int NQ, int MODE>
 constexpr int cell_min_ctas() {
   return sizeof(R) == 4 ? (MODE == 2 && NQ <= 3 ? 4 : (NQ == 4 ? 3 : CELL_MIN_CTAS_F32)) : 1;
 }
-template <class R, int ORDER, int NQ, int MODE, class Tin>
+template <class R, int ORDER, int NQ, int MODE, class Tin, class E = R>
 __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_ctas<R, NQ, MODE>()))
-    k_cell(const Tin* __restrict__ Qin, const R* __restrict__ G, const StageIO<R> io, const GasPar<R> gp,
+    k_cell(const Tin* __restrict__ Qin, const R* __restrict__ G, const StageIO<R, E> io, const GasPar<R> gp,
            const MeshDev m, const double dt, unsigned* __restrict__ flag) {
   using LY = CellLayout<ORDER, NQ>;
-  using S = CellSmem<R, ORDER, NQ, Tin>;
+  using S = CellSmem<R, ORDER, NQ, Tin, E>;
+  constexpr bool SPLIT = !std::is_same<E, R>::value;  // FP32 flux, FP64 epilogue
   constexpr int NM = LY::NM, NP = LY::NP, NC = S::NC, CB = LY::CB, PG = LY::PG, GW = LY::GW, NT = n_tmodes(ORDER);
   constexpr int NOUT = LY::NOUT, NOP = LY::NOP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R(*red)[GW][2][NOP] = reinterpret_cast<R(*)[GW][2][NOP]>(smem_raw + S::red_off);  // GW > 1 only
-  R* invM = reinterpret_cast<R*>(smem_raw + S::tab_off);
+  E* invM = reinterpret_cast<E*>(smem_raw + S::tab_off);
   int* tix = reinterpret_cast<int*>(invM + NM);  // [3][NM] tangential index, then [3][NM] parity sign
   const int tid = threadIdx.x, nthr = LY::WARPS * 32;
   const int lane = tid & 31, lg = lane % PG, warp = tid >> 5;
@@ -535,8 +543,8 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
   for (int e = tid; e < NM; e += nthr) {
     // (2a+1)(2b+1)(2c+1) / |K|; on a rectilinear mesh the 1/|K| of each cell
     // is applied in the epilogue
-    invM[e] = (R)((2 * mode_exp(e, 0) + 1) * (2 * mode_exp(e, 1) + 1) * (2 * mode_exp(e, 2) + 1)) *
-              (mesh_nonuniform(m) ? R(1) : mesh_ivol<R>(m));
+    invM[e] = (E)((2 * mode_exp(e, 0) + 1) * (2 * mode_exp(e, 1) + 1) * (2 * mode_exp(e, 2) + 1)) *
+              (mesh_nonuniform(m) ? E(1) : mesh_ivol<E>(m));
 #pragma unroll
     for (int D = 0; D < 3; ++D) {
       tix[D * NM + e] = tmode_index(mode_exp(e, tan1(D)), mode_exp(e, tan2(D)));
@@ -544,11 +552,11 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     }
   }
 
-  const R h = (R)dt, h2 = (R)(dt * dt);
+  const E h = (E)dt, h2 = (E)(dt * dt);
   // Everything after the staging of one tile (CB consecutive cells along x of
   // row (j, k)), reading the coefficients from coef[NC][CB].  With GW = 1 the
   // results go to so[kind][NC][CB] in shared memory (written out by flush).
-  auto tile = [&](const int i0, const int j, const int k, const R (*coef)[CB], R (*so)[NC][CB]) {
+  auto tile = [&](const int i0, const int j, const int k, const R (*coef)[CB], E (*so)[NC][CB]) {
     const size_t row = ((size_t)k * ny + j) * nx;
     // ---- interior flux of Eq. (flux-2) at this lane's Gauss point ----
     const bool active = (pidx < NP) && (i0 + cb < nx);
@@ -604,15 +612,16 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
 
     // One output (variable v, mode n) of the cell at x index i: the six faces'
     // moments with the sign/parity of Eq. (operator), M^-1, and the stage
-    // epilogue in the flux precision R; the accumulation into the stored FP64
-    // state is the one FP64 operation.
-    auto finish = [&](int v, int n, int i, int cc, R sF, R sT) {
+    // epilogue in the precision E; with E = R the accumulation into the
+    // stored FP64 state is the one FP64 operation.
+    auto finish = [&](int v, int n, int i, int cc, R sF_, R sT_) {
+      E sF = (E)sF_, sT = (E)sT_;
       const size_t cell = row + i;
       const size_t idx = (size_t)(v * NM + n) * nc + cell;
   #pragma unroll
       for (int D = 0; D < 3; ++D) {
         const int t = tix[D * NM + n];
-        const R sg = (R)tix[3 * NM + D * NM + n];
+        const E sg = (E)tix[3 * NM + D * NM + n];
         size_t up;
         if (D == 0)
           up = row + wrapm(i + 1, nx);
@@ -621,21 +630,24 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         else
           up = ((size_t)wrapm(k + 1, nz) * ny + j) * nx + i;
         const R* gD = G + (size_t)D * nc * (10 * NT) + v * NT + t;  // face-major: [D][face][10][NT]
-        sF += sg * gD[cell * (10 * NT)] - gD[up * (10 * NT)];
-        sT += sg * gD[cell * (10 * NT) + 5 * NT] - gD[up * (10 * NT) + 5 * NT];
+        sF += sg * (E)gD[cell * (10 * NT)] - (E)gD[up * (10 * NT)];
+        sT += sg * (E)gD[cell * (10 * NT) + 5 * NT] - (E)gD[up * (10 * NT) + 5 * NT];
       }
-      R iM = invM[n];
+      E iM = invM[n];
       if (mesh_nonuniform(m))  // 1/|K| = (2/h_x)(2/h_y)(2/h_z) / 8
-        iM *= cell_sc<R>(m, 0, i) * cell_sc<R>(m, 1, j) * cell_sc<R>(m, 2, k) * R(0.125);
-      const R Lv = sF * iM, Ltv = sT * iM;
+        iM *= cell_sc<E>(m, 0, i) * cell_sc<E>(m, 1, j) * cell_sc<E>(m, 2, k) * E(0.125);
+      const E Lv = sF * iM, Ltv = sT * iM;
       if constexpr (GW == 1) {
         const int o = v * NM + n;
         if (MODE == MODE_RESIDUAL) {
           so[0][o][cc] = Lv;
           so[1][o][cc] = Ltv;
         } else if (MODE == MODE_STAGE1) {
-          so[0][o][cc] = coef[o][cc] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
-          so[1][o][cc] = h * Lv + (h2 * R(1.0 / 6.0)) * Ltv;
+          if constexpr (SPLIT)  // the increment of Q* only; flush adds it to the FP64 state
+            so[0][o][cc] = E(0.5) * h * Lv + (h2 * E(0.125)) * Ltv;
+          else
+            so[0][o][cc] = coef[o][cc] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
+          so[1][o][cc] = h * Lv + (h2 * E(1.0 / 6.0)) * Ltv;
         } else {
           so[0][o][cc] = Ltv;
         }
@@ -643,10 +655,13 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         io.L[idx] = (double)Lv;
         io.Lt[idx] = (double)Ltv;
       } else if (MODE == MODE_STAGE1) {
-        io.Qs[idx] = coef[v * NM + n][cc] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
-        io.inc[idx] = h * Lv + (h2 * R(1.0 / 6.0)) * Ltv;
+        if constexpr (SPLIT)
+          io.Qs[idx] = (R)(io.Qn[idx] + (E(0.5) * h * Lv + (h2 * E(0.125)) * Ltv));
+        else
+          io.Qs[idx] = coef[v * NM + n][cc] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
+        io.inc[idx] = h * Lv + (h2 * E(1.0 / 6.0)) * Ltv;
       } else {
-        const double q = io.Qn[idx] + (double)(io.inc[idx] + (h2 * R(1.0 / 3.0)) * Ltv);
+        const double q = io.Qn[idx] + (double)(io.inc[idx] + (h2 * E(1.0 / 3.0)) * Ltv);
         io.Qn[idx] = q;
         if (io.Qf) io.Qf[idx] = (R)q;
       }
@@ -776,7 +791,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     };
     // outputs of tile tt (in so[bb]) -> global memory, a row of CB consecutive
     // cells per (variable, mode): whole sectors instead of one value per row
-    R(*so)[2][NC][CB] = reinterpret_cast<R(*)[2][NC][CB]>(smem_raw + S::out_off);
+    E(*so)[2][NC][CB] = reinterpret_cast<E(*)[2][NC][CB]>(smem_raw + S::out_off);
     auto flush = [&](long long tt, int bb) {
       const int i0 = (int)(tt % ntx) * CB;
       const size_t row = (size_t)(tt / ntx) * nx;
@@ -788,10 +803,13 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
           io.L[idx] = (double)so[bb][0][o][cc];
           io.Lt[idx] = (double)so[bb][1][o][cc];
         } else if (MODE == MODE_STAGE1) {
-          io.Qs[idx] = so[bb][0][o][cc];
+          if constexpr (SPLIT)
+            io.Qs[idx] = (R)(io.Qn[idx] + so[bb][0][o][cc]);
+          else
+            io.Qs[idx] = so[bb][0][o][cc];
           io.inc[idx] = so[bb][1][o][cc];
         } else {
-          const double q = io.Qn[idx] + (double)(io.inc[idx] + (h2 * R(1.0 / 3.0)) * so[bb][0][o][cc]);
+          const double q = io.Qn[idx] + (double)(io.inc[idx] + (h2 * E(1.0 / 3.0)) * so[bb][0][o][cc]);
           io.Qn[idx] = q;
           if (io.Qf) io.Qf[idx] = (R)q;
         }
@@ -871,10 +889,10 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
 // most one per tile) when a cell fits in one warp, otherwise one CTA per tile.
 // The persistent kernel strides over the tiles, so any grid size is correct;
 // if the occupancy query fails, one CTA per tile is launched.
-template <class R, int ORDER, int NQ, int MODE, class Tin>
+template <class R, int ORDER, int NQ, int MODE, class Tin, class E = R>
 inline void cell_launch_config(const MeshDev& m, dim3& grid, size_t& smem) {
   using LY = CellLayout<ORDER, NQ>;
-  smem = CellSmem<R, ORDER, NQ, Tin>::bytes;
+  smem = CellSmem<R, ORDER, NQ, Tin, E>::bytes;
   const long long ntx = (m.nx + LY::CB - 1) / LY::CB;
   if (LY::GW != 1) {
     grid = dim3((unsigned)ntx, (unsigned)m.ny, (unsigned)m.nz);
@@ -885,7 +903,7 @@ inline void cell_launch_config(const MeshDev& m, dim3& grid, size_t& smem) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) == cudaSuccess &&
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cell<R, ORDER, NQ, MODE, Tin>, LY::WARPS * 32, smem) ==
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cell<R, ORDER, NQ, MODE, Tin, E>, LY::WARPS * 32, smem) ==
           cudaSuccess &&
       sms > 0 && per > 0 && (long long)sms * per < g)
     g = (long long)sms * per;

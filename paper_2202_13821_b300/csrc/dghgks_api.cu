@@ -39,7 +39,8 @@ struct dghgks_ctx {
   void* Qs = nullptr;   // Q* (stage-1 output), flux precision
   void* Qf = nullptr;   // FP32-mixed: the state rounded to FP32 by a stage-2 pass, read by the
                         // next step's stage-1 kernels within one dghgks_steps / dghgks_run_host call
-  void* Inc = nullptr;  // dt L + dt^2/6 L_t (stage-1 output), flux precision
+  void* Inc = nullptr;  // dt L + dt^2/6 L_t (stage-1 output), epilogue precision (FP64 with
+                        // DGHGKS_FP32_STAGE64, else the flux precision)
   void* G = nullptr;      // face moments [3][cells][10][NT] (face-major), flux precision
   unsigned* flag = nullptr;
   double* part = nullptr;  // reduction partials [kRedBlocks][5]
@@ -155,10 +156,13 @@ struct Ops {
   void (*cell)(dghgks_ctx*, int, double*, double*, double*, double, cudaStream_t, bool copy_in, bool copy_out);
   void (*ek)(dghgks_ctx*, const double*, cudaStream_t);
   void (*enstrophy)(dghgks_ctx*, const double*, cudaStream_t);
-  size_t r_size;
+  size_t r_size;  // flux precision: Q*, the FP32 state copy, face moments
+  size_t e_size;  // epilogue precision: the stage increment inc
 };
 
-template <class R, int ORDER, int NQ>
+// E: precision of the cell kernels' epilogue (E = R, or double with R = float
+// for the FP32-flux / FP64-stage contexts)
+template <class R, int ORDER, int NQ, class E = R>
 struct Impl {
   using FS = FaceSmem<R, ORDER, NQ>;
 
@@ -175,10 +179,10 @@ struct Impl {
     DG_ATTR((k_face<R, ORDER, NQ, 0, R, true>), FS::bytes)
     DG_ATTR((k_face<R, ORDER, NQ, 1, R, true>), FS::bytes)
     DG_ATTR((k_face<R, ORDER, NQ, 2, R, true>), FS::bytes)
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_RESIDUAL, double>), (CellSmem<R, ORDER, NQ, double>::bytes))
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, double>), (CellSmem<R, ORDER, NQ, double>::bytes))
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, R>), (CellSmem<R, ORDER, NQ, R>::bytes))
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE2, R>), (CellSmem<R, ORDER, NQ, R>::bytes))
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_RESIDUAL, double, E>), (CellSmem<R, ORDER, NQ, double, E>::bytes))
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, double, E>), (CellSmem<R, ORDER, NQ, double, E>::bytes))
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, R, E>), (CellSmem<R, ORDER, NQ, R, E>::bytes))
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE2, R, E>), (CellSmem<R, ORDER, NQ, R, E>::bytes))
 #undef DG_ATTR
     return e;
   }
@@ -215,12 +219,13 @@ struct Impl {
   }
 
   template <int MODE, class Tin>
-  static void cell_t(dghgks_ctx* c, const Tin* Qin, const R* G, const StageIO<R>& io, const GasPar<R>& g,
+  static void cell_t(dghgks_ctx* c, const Tin* Qin, const R* G, const StageIO<R, E>& io, const GasPar<R>& g,
                      const MeshDev& m, double dt, cudaStream_t s) {
     dim3 grid;
     size_t smem = 0;
-    cell_launch_config<R, ORDER, NQ, MODE, Tin>(m, grid, smem);
-    k_cell<R, ORDER, NQ, MODE, Tin><<<grid, CellLayout<ORDER, NQ>::WARPS * 32, smem, s>>>(Qin, G, io, g, m, dt, c->flag);
+    cell_launch_config<R, ORDER, NQ, MODE, Tin, E>(m, grid, smem);
+    k_cell<R, ORDER, NQ, MODE, Tin, E>
+        <<<grid, CellLayout<ORDER, NQ>::WARPS * 32, smem, s>>>(Qin, G, io, g, m, dt, c->flag);
   }
 
   static void cell(dghgks_ctx* c, int mode, double* Q, double* L, double* Lt, double dt, cudaStream_t s,
@@ -228,11 +233,11 @@ struct Impl {
     const GasPar<R> g = gas_par<R>(c, dt);
     const MeshDev m = mesh_dev(c);
     const R* G = static_cast<const R*>(c->G);
-    StageIO<R> io;
+    StageIO<R, E> io;
     io.L = L;
     io.Lt = Lt;
     io.Qs = static_cast<R*>(c->Qs);
-    io.inc = static_cast<R*>(c->Inc);
+    io.inc = static_cast<E*>(c->Inc);
     io.Qn = Q;
     io.Qf = copy_out ? static_cast<R*>(c->Qf) : nullptr;
     ProfScope ps(c, 3 + mode, s);
@@ -260,16 +265,18 @@ struct Impl {
   }
 };
 
-template <class R, int O, int N>
+template <class R, int O, int N, class E = R>
 constexpr Ops make_ops() {
-  return Ops{&Impl<R, O, N>::set_attrs,
-             &Impl<R, O, N>::faces,
-             &Impl<R, O, N>::cell,
-             &Impl<R, O, N>::ek,
-             &Impl<R, O, N>::enstrophy,
-             sizeof(R)};
+  return Ops{&Impl<R, O, N, E>::set_attrs,
+             &Impl<R, O, N, E>::faces,
+             &Impl<R, O, N, E>::cell,
+             &Impl<R, O, N, E>::ek,
+             &Impl<R, O, N, E>::enstrophy,
+             sizeof(R),
+             sizeof(E)};
 }
 #define DG_OPS(R, O, N) make_ops<R, O, N>()
+#define DG_OPS_STAGE64(O, N) make_ops<float, O, N, double>()
 
 const Ops kOps64_1_2 = DG_OPS(double, 1, 2);
 const Ops kOps64_2_2 = DG_OPS(double, 2, 2);
@@ -281,14 +288,24 @@ const Ops kOps64_3_3 = DG_OPS(double, 3, 3);
 const Ops kOps64_3_4 = DG_OPS(double, 3, 4);
 const Ops kOps32_3_3 = DG_OPS(float, 3, 3);
 const Ops kOps32_3_4 = DG_OPS(float, 3, 4);
+const Ops kOps32s_1_2 = DG_OPS_STAGE64(1, 2);
+const Ops kOps32s_2_2 = DG_OPS_STAGE64(2, 2);
+const Ops kOps32s_2_3 = DG_OPS_STAGE64(2, 3);
+const Ops kOps32s_3_3 = DG_OPS_STAGE64(3, 3);
+const Ops kOps32s_3_4 = DG_OPS_STAGE64(3, 4);
 
 const Ops* select_ops(int precision, int order, int nq) {
-  const bool f64 = precision == DGHGKS_FP64;
-  if (order == 1 && nq == 2) return f64 ? &kOps64_1_2 : &kOps32_1_2;
-  if (order == 2 && nq == 2) return f64 ? &kOps64_2_2 : &kOps32_2_2;
-  if (order == 2 && nq == 3) return f64 ? &kOps64_2_3 : &kOps32_2_3;
-  if (order == 3 && nq == 3) return f64 ? &kOps64_3_3 : &kOps32_3_3;
-  if (order == 3 && nq == 4) return f64 ? &kOps64_3_4 : &kOps32_3_4;
+  const int p = precision == DGHGKS_FP64 ? 0 : (precision == DGHGKS_FP32_MIXED ? 1 : 2);
+  const Ops* const tab[5][3] = {{&kOps64_1_2, &kOps32_1_2, &kOps32s_1_2},
+                                {&kOps64_2_2, &kOps32_2_2, &kOps32s_2_2},
+                                {&kOps64_2_3, &kOps32_2_3, &kOps32s_2_3},
+                                {&kOps64_3_3, &kOps32_3_3, &kOps32s_3_3},
+                                {&kOps64_3_4, &kOps32_3_4, &kOps32s_3_4}};
+  if (order == 1 && nq == 2) return tab[0][p];
+  if (order == 2 && nq == 2) return tab[1][p];
+  if (order == 2 && nq == 3) return tab[2][p];
+  if (order == 3 && nq == 3) return tab[3][p];
+  if (order == 3 && nq == 4) return tab[4][p];
   return nullptr;
 }
 
@@ -387,8 +404,8 @@ int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, dou
   const int nq = (opts && opts->n_q) ? opts->n_q : order + 1;
   const int precision = opts ? opts->precision : DGHGKS_FP64;
   const double tau_eps = opts ? opts->tau_eps : 0.0;
-  if (precision != DGHGKS_FP64 && precision != DGHGKS_FP32_MIXED)
-    return fail(nullptr, DGHGKS_EARG, "precision must be DGHGKS_FP64 or DGHGKS_FP32_MIXED");
+  if (precision != DGHGKS_FP64 && precision != DGHGKS_FP32_MIXED && precision != DGHGKS_FP32_STAGE64)
+    return fail(nullptr, DGHGKS_EARG, "precision must be DGHGKS_FP64, DGHGKS_FP32_MIXED or DGHGKS_FP32_STAGE64");
   if (!(tau_eps >= 0.0)) return fail(nullptr, DGHGKS_EARG, "tau_eps must be >= 0");
   const Ops* ops = select_ops(precision, order, nq);
   if (!ops) return fail(nullptr, DGHGKS_EUNSUP, "unsupported order %d with n_q %d", order, nq);
@@ -438,11 +455,12 @@ int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, dou
   c->ops = ops;
 
   const size_t stage = ops->r_size * 5 * (size_t)c->nm * c->ncell;
+  const size_t stage_inc = ops->e_size * 5 * (size_t)c->nm * c->ncell;
   const size_t gbytes = ops->r_size * 30 * (size_t)c->nt * c->ncell;
   int rc = DGHGKS_OK;
   if (!rc) rc = cuda_check(c, ops->set_attrs(), "cudaFuncSetAttribute");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->Qs, stage), "cudaMalloc(Q*)");
-  if (!rc) rc = cuda_check(c, cudaMalloc(&c->Inc, stage), "cudaMalloc(stage increment)");
+  if (!rc) rc = cuda_check(c, cudaMalloc(&c->Inc, stage_inc), "cudaMalloc(stage increment)");
   if (!rc && precision != DGHGKS_FP64) rc = cuda_check(c, cudaMalloc(&c->Qf, stage), "cudaMalloc(FP32 state copy)");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->G, gbytes), "cudaMalloc(face moments)");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->flag, sizeof(unsigned)), "cudaMalloc(flag)");

@@ -138,8 +138,9 @@ def test_p3_residual(torch, api, orc, nq, state):
     assert_residual_parity(L, Lt, ref)
 
 
+@pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("order,nq", [(1, 2), (2, 2), (2, 3), (3, 3), (3, 4)])
-def test_fp32_mixed_residual_every_layout(torch, api, orc, order, nq):
+def test_fp32_mixed_residual_every_layout(torch, api, orc, order, nq, precision):
     """FP32-mixed residual (Sec. 3, Eq. (flux) and (flux-2) in FP32 arithmetic) against the FP64
     oracle for every FP32 face layout (a thread per row of n_q Gauss points) and cell layout, on a
     perturbed Taylor-Green state with 35 cells along x (one full 32-face CTA and a ragged one).
@@ -149,11 +150,12 @@ def test_fp32_mixed_residual_every_layout(torch, api, orc, order, nq):
     of the projections to 6e-8 of its size; 2e-5 = 335 units of FP32 rounding of the scale leaves
     room for their accumulation and for the divisions and exponentials of the flux.  Measured on a
     B300: L within 2.5e-7 of its scale for every layout; L_t, formed from the time fit of the face
-    flux, within 1.6e-5 at P1 (the fewest terms per scale), 9e-6 at P2 and 5e-6 at P3."""
+    flux, within 1.6e-5 at P1 (the fewest terms per scale), 9e-6 at P2 and 5e-6 at P3.  The same
+    bound holds for the FP32 flux with FP64 assembly and M^-1 (precision 2)."""
     from paper_2202_13821_b300 import inputs
 
     n = (35, 5, 3)
-    s, pb = make(api, orc, n, order=order, nq=nq, mu=1 / 1600, Pr=0.72, precision=1, **TGV)
+    s, pb = make(api, orc, n, order=order, nq=nq, mu=1 / 1600, Pr=0.72, precision=precision, **TGV)
     Q = inputs.modal_state(inputs.tgv_prim, n, order, TGV["lo"], TGV["hi"], perturb=1e-3)
     L, Lt, ref = residual_pair(torch, s, pb, orc, Q, 1.5e-3)
     worst = []
@@ -162,7 +164,7 @@ def test_fp32_mixed_residual_every_layout(torch, api, orc, order, nq):
         scale = np.abs(sc).reshape(5, -1).max(axis=1)
         worst.append((err / scale).max())
         assert np.all(err <= 2e-5 * scale), err / scale
-    print(f"P{order} n_q={nq}: max err / scale L {worst[0]:.2e}, L_t {worst[1]:.2e}")
+    print(f"P{order} n_q={nq} precision {precision}: max err / scale L {worst[0]:.2e}, L_t {worst[1]:.2e}")
 
 
 @pytest.mark.parametrize("order,nq,case", [(1, 2, "adv"), (2, 3, "tgv"), (3, 4, "tgv")])
@@ -212,10 +214,11 @@ def test_sampled_cells_full_size_tgv_256(torch, api, orc):
         assert np.all(err <= RTOL * scale), err / scale
 
 
-def test_fp32_mixed_steps_sampled_full_size_tgv_256(torch, api, orc):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_fp32_mixed_steps_sampled_full_size_tgv_256(torch, api, orc, precision):
     """Bench configuration of the timed leg (TGV 256^3, P2, n_q = 3, FP32-mixed, one dghgks_steps call
     of 2 steps, the second reading the FP32 copy of the state) against the FP64 oracle on sampled
-    cells.  After 2 S2O4 steps (4 stages) a cell depends only on the cells within 4 face-neighbour
+    cells; the same for the FP32 flux with FP64 stage arithmetic (precision 2).  After 2 S2O4 steps (4 stages) a cell depends only on the cells within 4 face-neighbour
     hops, so the oracle steps a periodic 9^3 box cut around each sampled cell from the same initial
     state; the box's wrap reaches the centre only after 5 hops, so the centre's result is exact.
 
@@ -226,7 +229,7 @@ def test_fp32_mixed_steps_sampled_full_size_tgv_256(torch, api, orc):
     from paper_2202_13821_b300 import inputs
 
     n = 256
-    s = api.Solver((n,) * 3, TGV["lo"], TGV["hi"], order=2, mu=1 / 1600, Pr=0.72, n_q=3, precision=1)
+    s = api.Solver((n,) * 3, TGV["lo"], TGV["hi"], order=2, mu=1 / 1600, Pr=0.72, n_q=3, precision=precision)
     Q0 = inputs.tgv_state(n, 2, device="cuda")
     dt = inputs.tgv_dt(n, 2)
     Qd = Q0.clone()
@@ -249,7 +252,8 @@ def test_fp32_mixed_steps_sampled_full_size_tgv_256(torch, api, orc):
         err = np.abs(got - want).max(axis=1)
         assert np.all(err <= tol), (i, j, k, err / tol)
         worst = np.maximum(worst, err / tol)
-    print("max error / tolerance per variable:", worst)
+    s.close()
+    print(f"precision {precision}: max error / tolerance per variable:", worst)
 
 
 def test_totals_and_kinetic_energy(torch, api, orc):

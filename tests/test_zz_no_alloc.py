@@ -4,12 +4,14 @@ Callers inside another framework's memory plan, real-time loops that forbid
 allocation after start-up, or code that must not trigger cudaFree's device
 synchronisation cannot create a context (dghgks_init allocates).  This entry
 point keeps its scratch in a fixed device array instead.  The test calls it
-twice in a row through the C ABI and compares both results with the
-context-based dghgks_residual at the tolerance of the other residual tests
-(relative 1e-11 per variable; the kernels are the same, so the results are in
-fact identical), and checks that an oversized problem is refused before any
-GPU work.  This file is collected last so that a failure here cannot hide the
-other tests.
+twice in a row through the C ABI for every supported layout (P1 with n_q = 2,
+P2 with n_q = 2 and 3) in FP64 and FP32-mixed, on a grid whose x extent is
+not a multiple of the face kernel's 32-face tiles, and requires both results
+to equal the context-based dghgks_residual bit for bit: the same kernels run
+on the same inputs.  The tolerance of the other residual tests (relative
+1e-11) is asserted as well, so that a mismatch also reports its size.  It also
+checks that an oversized problem is refused before any GPU work.  This file is
+collected last so that a failure here cannot hide the other tests.
 """
 import math
 
@@ -28,7 +30,8 @@ def per_var_err(a, b):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("precision", [0, 1])
-def test_static_residual_matches_context_residual_twice(precision):
+@pytest.mark.parametrize("order,nq", [(1, 2), (2, 2), (2, 3)])
+def test_static_residual_matches_context_residual_twice(order, nq, precision):
     import torch
 
     if not torch.cuda.is_available():
@@ -36,20 +39,21 @@ def test_static_residual_matches_context_residual_twice(precision):
     from paper_2202_13821_b300 import api, build, inputs
 
     build.build()
-    n, lo, hi = (13, 9, 7), (-math.pi,) * 3, (math.pi,) * 3
-    kw = dict(order=2, gamma=1.4, mu=1 / 1600, Pr=0.72)
-    Q = inputs.tgv_state(n, 2, perturb=1e-3, device="cuda")
-    s = api.Solver(n, lo, hi, n_q=3, precision=precision, **kw)
+    n, lo, hi = (37, 9, 7), (-math.pi,) * 3, (math.pi,) * 3
+    kw = dict(order=order, gamma=1.4, mu=1 / 1600, Pr=0.72)
+    Q = inputs.tgv_state(n, order, perturb=1e-3, device="cuda")
+    s = api.Solver(n, lo, hi, n_q=nq, precision=precision, **kw)
     L0, Lt0 = s.residual(Q, 1.3e-3)
     torch.cuda.synchronize()
-    ref = (L0.cpu().numpy(), Lt0.cpu().numpy())
+    s.close()
     for _ in range(2):
         L = torch.full_like(Q, float("nan"))
         Lt = torch.full_like(Q, float("nan"))
         api.dghgks_residual_static(n, lo, hi, kw["order"], kw["gamma"], kw["mu"], kw["Pr"], Q, 1.3e-3, L, Lt,
-                                   n_q=3, precision=precision)
-        for got, want in zip((L.cpu().numpy(), Lt.cpu().numpy()), ref):
-            assert per_var_err(got, want).max() < RTOL
+                                   n_q=nq, precision=precision)
+        for got, want in ((L, L0), (Lt, Lt0)):
+            assert per_var_err(got.cpu().numpy(), want.cpu().numpy()).max() < RTOL
+            assert torch.equal(got, want)
 
 
 @pytest.mark.gpu
