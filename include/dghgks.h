@@ -97,7 +97,8 @@ typedef struct {
  * n_q = 2 or 3; order 3 with n_q = 3 or 4) on `mesh`, for a gas with ratio of specific heats gamma, viscosity
  * mu >= 0 and Prandtl number Pr > 0 (Pr = 1 is the BGK value used by the
  * paper; Pr != 1 adds (1/Pr - 1) times the heat flux of the same distribution
- * to the energy flux, which the paper does not define).  opts may be NULL
+ * to the energy flux F at t_n, not to its time derivative F_t, which the
+ * paper does not define).  opts may be NULL
  * (n_q = order+1, FP64, tau_eps = 0).  Uses the current CUDA device.
  * Allocates the scratch: 2 stage buffers with the state's values in the flux
  * precision (Q* and the stage increment; the increment in FP64 with

@@ -19,8 +19,9 @@ interface flux of Eq. (flux) is pinned at continuous states by its Euler and
 Navier-Stokes limits and at discontinuous states by a brute-force
 velocity/time quadrature of the distribution it integrates
 (``tests/test_oracle_flux_quadrature.py``).  The Prandtl-number correction
-(Pr != 1) is a reading, since the paper does not define it; its F and F_t
-arithmetic is pinned by that same quadrature of the definition taken.
+(Pr != 1) is a reading, since the paper does not define it: it acts on F
+only (see the header of dghgks_oracle.hpp), and its arithmetic is pinned by
+that same quadrature of the definition taken.
 """
 from __future__ import annotations
 

@@ -35,13 +35,18 @@
 //   * The time fit of Eq. (expansion-1) is applied to the time-integral weight
 //     of each moment term of Eq. (flux) (the integrals are linear in those
 //     weights); the difference T(dt) - 2 T(dt/2) is evaluated in factored form.
-//   * Prandtl number: Pr != 1 adds (1/Pr - 1) q to the energy flux, with
-//     q = 1/2 <(u_n - U_n)(|u-U|^2 + xi^2) f> the heat flux of the same f
-//     (not in the paper, whose Taylor-Green case has Pr = 1).  The definition
-//     is a reading: the paper fixes no value for this term.  Its arithmetic is
-//     pinned: F against the Navier-Stokes heat flux at continuous states, F
-//     and F_t against a brute-force velocity/time quadrature of the same
-//     definition at discontinuous states (tests/test_oracle_flux_quadrature.py).
+//   * Prandtl number: Pr != 1 adds (1/Pr - 1) q to the energy flux F (not to
+//     F_t), with q = 1/2 <(u_n - U_n)(|u-U|^2 + xi^2) f> the heat flux of the
+//     same f fitted at t_n (not in the paper, whose Taylor-Green case has
+//     Pr = 1).  q is taken about the velocity U_n of t_n; the part of f
+//     linear in t shifts the mean velocity, so a fitted time derivative of q
+//     would hold a frame-shift term in d_t U that is not a heat flux (with it
+//     the P2 Taylor-Green run at Pr = 0.72 grew its high modes without
+//     bound).  The definition is a reading: the paper fixes no value for this
+//     term.  Its arithmetic is pinned: F against the Navier-Stokes heat flux
+//     at continuous states, F at discontinuous states against a brute-force
+//     velocity/time quadrature of the same definition
+//     (tests/test_oracle_flux_quadrature.py).
 #pragma once
 #include <cmath>
 #include <cstdint>
@@ -566,10 +571,7 @@ inline bool face_flux_local(const T QL[5], const T dQL[3][5], const T QR[5], con
     H[4] = gl.rho * moment(l_pos, {&h, &alu}) + gr.rho * moment(r_neg, {&h, &aru});
     H[5] = gl.rho * moment(l_pos, {&h, &Alp}) + gr.rho * moment(r_neg, {&h, &Arp});
     double c = 1.0 / ph.Pr - 1.0;
-    for (int j = 0; j < 6; ++j) {
-      F[4] += c * wF[j] * H[j];
-      Ft[4] += c * wFt[j] * H[j];
-    }
+    for (int j = 0; j < 6; ++j) F[4] += c * wF[j] * H[j];
   }
   return true;
 }
@@ -644,7 +646,6 @@ inline bool cell_flux(const T Q[5], const T dQ[3][5], const Phys<T>& ph, double 
       T q1 = moment(all, {&h, &au});
       T q2 = moment(all, {&h, &Ap});
       F[d][4] += c * g.rho * (q0 - tau * (q1 + q2));
-      Ft[d][4] += c * g.rho * q2;
     }
   }
   return true;

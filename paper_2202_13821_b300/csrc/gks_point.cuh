@@ -10,10 +10,15 @@
 //     f = g0 (1 - tau (a.u + A) + A t), which is linear in t: F = F(0),
 //     F_t = rho <u_d A psi>.
 //   * tau = mu / p + tau_eps dt (Sec. 3, Remark 1).
-//   * Pr != 1 (not in the paper): the energy flux gains (1/Pr - 1) q, where
-//     q = 1/2 <(u_n - U_n)(|u - U|^2 + xi^2) f> is evaluated from the flux
-//     moments F = <u_n psi phi> and density moments W = <psi phi> of each
-//     term phi of f.
+//   * Pr != 1 (not in the paper): the energy flux F (not F_t) gains
+//     (1/Pr - 1) q, where q = 1/2 <(u_n - U_n)(|u - U|^2 + xi^2) f> is
+//     evaluated from the flux moments F = <u_n psi phi> and density moments
+//     W = <psi phi> of each term phi of f.  The correction is fitted at t_n
+//     only: q is taken about the velocity U of t_n, and the part of f that
+//     grows linearly in t moves its mean velocity, so the fitted time
+//     derivative of q would carry a frame-shift term proportional to d_t U
+//     (not a heat flux); with it the P2 scheme grew its high modes without
+//     bound at Pr = 0.72.
 //
 // Implementation choices (B300): moment indices are template parameters so
 // every moment product is resolved at compile time; the 5x5 slope systems are
@@ -638,7 +643,6 @@ DG_HD bool iface_finish(const SideSums<R>& S, const GasPar<R>& g, R F[5], R Ft[5
     const R H5 = V5[4] - U * c4(S.W5);
     const R H6 = V6[4] - U * c4(S.W6);
     Fc[4] += g.pr_fix * (wF[1] * H2 + wF[2] * H3 + wF[3] * H4 + wF[4] * H5 + wF[5] * H6);
-    Ftc[4] += g.pr_fix * (wFt[1] * H2 + wFt[2] * H3 + wFt[3] * H4 + wFt[4] * H5 + wFt[5] * H6);
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) F[k] = Ft[k] = R(0);
@@ -690,10 +694,10 @@ DG_HD void interior_dir(const CTab<R>& t, const Prim<R>& p, R hs2, const R a[3][
   if (g.pr_fix != R(0)) {
     // heat moments about U of the terms (a . u) g and A g: component 4 of
     // <u_d psi'' phi> - U_d <psi'' phi>, with <psi'' (a . u) g> = Wau'' and <psi'' A g> = -Wau''
+    // (F only: the t A g term's heat moment about the U of t_n is the frame shift of g)
     const R H1 = m1[4] - Ud * Wau[4];
     const R H2 = m2[4] + Ud * Wau[4];
     Fc[4] += g.pr_fix * p.rho * (-tau * (H1 + H2));
-    Ftc[4] += g.pr_fix * p.rho * H2;
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) F[k] = Ft[k] = R(0);

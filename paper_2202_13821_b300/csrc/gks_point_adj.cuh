@@ -605,7 +605,6 @@ DG_HD void iface_finish_b(const SideSums<R>& S, const GasPar<R>& g, const R Fb[5
     H[4] = V5[4] - U * cen4(S.W5, U, V, W, hs2);
     H[5] = V6[4] - U * cen4(S.W6, U, V, W, hs2);
     Fc[4] += g.pr_fix * (wF[1] * H[1] + wF[2] * H[2] + wF[3] * H[3] + wF[4] * H[4] + wF[5] * H[5]);
-    Ftc[4] += g.pr_fix * (wFt[1] * H[1] + wFt[2] * H[2] + wFt[3] * H[3] + wFt[4] * H[4] + wFt[5] * H[5]);
   }
 
   // backward sweep
@@ -631,9 +630,8 @@ DG_HD void iface_finish_b(const SideSums<R>& S, const GasPar<R>& g, const R Fb[5
     R Hb[6];
 #pragma unroll
     for (int j = 1; j < 6; ++j) {
-      Hb[j] = g.pr_fix * (wF[j] * Fcb[4] + wFt[j] * Ftcb[4]);
+      Hb[j] = g.pr_fix * wF[j] * Fcb[4];
       wFb[j] += g.pr_fix * Fcb[4] * H[j];
-      wFtb[j] += g.pr_fix * Ftcb[4] * H[j];
     }
     r0b += Hb[1] * (V2[4] - U * Wab[4]) + Hb[2] * (V3[4] + U * Wab[4]);
     V2b[4] += Hb[1] * r0;
@@ -774,7 +772,6 @@ DG_HD void interior_dir_b(const CTab<R>& t, const Prim<R>& p, R hs2, const R a[3
     H1 = m1[4] - Ud * Wau[4];
     H2 = m2[4] + Ud * Wau[4];
     Fc[4] += g.pr_fix * p.rho * (-tau * (H1 + H2));
-    Ftc[4] += g.pr_fix * p.rho * H2;
   }
   // backward
   R Udb = R(0);
@@ -786,8 +783,8 @@ DG_HD void interior_dir_b(const CTab<R>& t, const Prim<R>& p, R hs2, const R a[3
   for (int k = 0; k < 5; ++k) m0b[k] = m1b[k] = m2b[k] = R(0);
   if (pr_fix) {
     const R H1b = -g.pr_fix * p.rho * tau * Fcb[4];
-    const R H2b = -g.pr_fix * p.rho * tau * Fcb[4] + g.pr_fix * p.rho * Ftcb[4];
-    pb.rho += g.pr_fix * (-tau * (H1 + H2) * Fcb[4] + H2 * Ftcb[4]);
+    const R H2b = -g.pr_fix * p.rho * tau * Fcb[4];
+    pb.rho += g.pr_fix * (-tau * (H1 + H2) * Fcb[4]);
     taub += -g.pr_fix * p.rho * (H1 + H2) * Fcb[4];
     m1b[4] += H1b;
     m2b[4] += H2b;

@@ -22,8 +22,9 @@ Eq. (flux) is evaluated explicitly at every node.
 * F(t) = sum over nodes of u psi f(t, node) for t at Gauss-Legendre nodes of
   [0, dt] and [0, dt/2]; the linear fit of Eq. (expansion-1) then gives F and
   F_t.  With Pr != 1 the heat flux q(t) = 1/2 <(u - U_0)(|u - U_0|^2 + xi^2) f>
-  of the same f, fitted alike, adds (1/Pr - 1) q to the energy flux (the
-  reading of the Prandtl correction that the oracle takes).
+  of the same f, fitted alike, adds (1/Pr - 1) q(t_n) to the energy flux F
+  and nothing to F_t (the reading of the Prandtl correction that the oracle
+  takes: the fitted slope of q about the fixed U_0 would be a frame shift).
 
 At discontinuous states with tau > 0 the side terms of Eq. (flux), which
 carry the side slopes a^l_i, A^l, a^r_i, A^r, differ from their equilibrium
@@ -172,9 +173,8 @@ def face_flux_quadrature(QL, dQL, QR, dQR, mu, Pr, tau_eps, dt):
     sol = np.linalg.solve(S, np.stack([I1, Ih]))
     F, Ft = sol[0], sol[1]
     if Pr != 1.0:
-        q, qt = np.linalg.solve(S, [H1, Hh])
+        q, _ = np.linalg.solve(S, [H1, Hh])
         F[4] += (1 / Pr - 1) * q
-        Ft[4] += (1 / Pr - 1) * qt
     return F, Ft
 
 
