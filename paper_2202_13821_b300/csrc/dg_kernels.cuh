@@ -423,7 +423,7 @@ struct CellLayout {
   static_assert(NP <= 64, "k_cell handles up to 4^3 points per cell");
 };
 
-template <class R, int ORDER, int NQ, class Tin = R, class E = R>
+template <class R, int ORDER, int NQ, class Tin = R, class E = R, int MODE = MODE_RESIDUAL>
 struct CellSmem {
   using LY = CellLayout<ORDER, NQ>;
   static constexpr int NM = LY::NM, NC = 5 * NM, CB = LY::CB;
@@ -437,9 +437,19 @@ struct CellSmem {
   // GW = 1: the outputs of a tile (two kinds, NC x CB), double-buffered, so
   // that they leave as rows of CB consecutive cells
   static constexpr size_t out = LY::GW == 1 ? sizeof(E) * 2 * 2 * NC * CB : 0;
+  // one cell per warp (n_q = 3): the volume projection is transposed through
+  // shared memory, a row per Gauss point and warp holding the point's
+  // contributions to 32 outputs, (F, F_t) pairs (F_t alone at stage 2); the
+  // row stride is padded by 16 bytes (conflict-free 16-byte stores along a
+  // row and 8-byte loads down a column)
+  static constexpr bool TRANS = LY::GW == 1 && LY::PG == 32;
+  static constexpr int TS = (MODE == MODE_STAGE2 ? 32 : 64) + 16 / (int)sizeof(R);
+  static constexpr size_t tr = TRANS ? sizeof(R) * LY::WARPS * LY::NP * TS : 0;
   static constexpr size_t tabs = sizeof(E) * NM + sizeof(int) * 6 * NM;
-  static constexpr size_t cvt_off = raw, red_off = raw + cvt, out_off = raw + cvt + red, tab_off = out_off + out;
-  static constexpr size_t bytes = raw + cvt + red + out + tabs;
+  static constexpr size_t cvt_off = raw, red_off = raw + cvt, out_off = raw + cvt + red, tr_off = out_off + out,
+                          tab_off = tr_off + tr;
+  static constexpr size_t bytes = raw + cvt + red + out + tr + tabs;
+  static_assert(tr_off % 16 == 0 && tr % 16 == 0, "16-byte aligned transpose rows");
 };
 
 // Recursive-halving butterfly over the PG lanes of a group: in[N] per lane ->
@@ -524,7 +534,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     k_cell(const Tin* __restrict__ Qin, const R* __restrict__ G, const StageIO<R, E> io, const GasPar<R> gp,
            const MeshDev m, const double dt, unsigned* __restrict__ flag) {
   using LY = CellLayout<ORDER, NQ>;
-  using S = CellSmem<R, ORDER, NQ, Tin, E>;
+  using S = CellSmem<R, ORDER, NQ, Tin, E, MODE>;
   constexpr bool SPLIT = !std::is_same<E, R>::value;  // FP32 flux, FP64 epilogue
   constexpr int NM = LY::NM, NP = LY::NP, NC = S::NC, CB = LY::CB, PG = LY::PG, GW = LY::GW, NT = n_tmodes(ORDER);
   constexpr int NOUT = LY::NOUT, NOP = LY::NOP;
@@ -680,22 +690,107 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     };
 
     if constexpr (GW == 1) {
-      // ---- volume projection fused with the epilogue: the PG lanes of a cell
-      // reduce PG volume outputs (modes n >= 1, j = v (NM-1) + n-1) at a time
-      // by a butterfly, after which lane lg holds output j = blk PG + lg of
-      // both kinds (F and F_t) and finishes it.  When the last block of RM
-      // outputs fits twice into PG slots, its F and F_t sums share one
-      // butterfly (F in slots 0..RM-1, F_t in RM..2RM-1) and a shuffle pairs
-      // them.  The five mode-0 outputs have face terms only.  No cross-warp
-      // exchange, no second barrier. ----
-      constexpr int NV = 5 * (NM - 1), NB = NV / PG, RM = NV % PG;
-      constexpr bool PACK = MODE != MODE_STAGE2 && RM > 0 && 2 * RM <= PG;
-      constexpr int NBLK = NB + ((RM > 0 && !PACK) ? 1 : 0);
-      constexpr bool M0_LAST = RM > 0 && RM + 5 <= PG;  // mode 0 on the idle lanes of the last pass
+      // ---- volume projection fused with the epilogue: the volume outputs
+      // (modes n >= 1, j = v (NM-1) + n-1) are summed over the cell's lanes a
+      // block at a time, after which lane lg holds output j of both kinds (F
+      // and F_t) and finishes it; the five mode-0 outputs have face terms
+      // only.  No cross-warp exchange, no CTA barrier. ----
+      constexpr int NV = 5 * (NM - 1);
       const bool live = i0 + cb < nx;
       auto vslot = [&](const R(&Fk)[3][5], int j) {
         return j < NV ? vol_term(Fk, (j / (NM - 1)) * NM + 1 + j % (NM - 1)) : R(0);
       };
+      if constexpr (PG == 32) {
+        // one cell per warp: for each block of 32 outputs every lane with a
+        // Gauss point writes its contributions as one shared-memory row, and
+        // lane lg sums column lg over the cell's points in a fixed order
+        // (packed FP32 pairs: F and F_t of one output side by side).  No
+        // shuffles and no lane-dependent selects.
+        constexpr int NBLK = (NV + 31) / 32, RM = NV - (NBLK - 1) * 32;
+        constexpr bool M0_LAST = RM + 5 <= 32;  // mode 0 on the idle lanes of the last pass
+        constexpr bool TWO = MODE != MODE_STAGE2;
+        constexpr int TS = S::TS;
+        R* const trows = reinterpret_cast<R*>(smem_raw + S::tr_off) + (size_t)warp * NP * TS;
+  #pragma unroll
+        for (int blk = 0; blk < NBLK; ++blk) {
+          const int nsl = blk == NBLK - 1 ? RM : 32;  // output slots of this block
+          if (pidx < NP) {
+            R* const row = trows + pidx * TS;
+            if constexpr (TWO && sizeof(R) == 4) {
+  #pragma unroll
+              for (int q = 0; q < 16; ++q)
+                if (2 * q < nsl)
+                  reinterpret_cast<float4*>(row)[q] =
+                      make_float4(vslot(Fw, blk * 32 + 2 * q), vslot(Ftw, blk * 32 + 2 * q),
+                                  vslot(Fw, blk * 32 + 2 * q + 1), vslot(Ftw, blk * 32 + 2 * q + 1));
+            } else if constexpr (TWO) {
+  #pragma unroll
+              for (int q = 0; q < 32; ++q)
+                if (q < nsl)
+                  reinterpret_cast<double2*>(row)[q] = make_double2(vslot(Fw, blk * 32 + q), vslot(Ftw, blk * 32 + q));
+            } else if constexpr (sizeof(R) == 4) {
+  #pragma unroll
+              for (int q = 0; q < 8; ++q)
+                if (4 * q < nsl)
+                  reinterpret_cast<float4*>(row)[q] =
+                      make_float4(vslot(Ftw, blk * 32 + 4 * q), vslot(Ftw, blk * 32 + 4 * q + 1),
+                                  vslot(Ftw, blk * 32 + 4 * q + 2), vslot(Ftw, blk * 32 + 4 * q + 3));
+            } else {
+  #pragma unroll
+              for (int q = 0; q < 16; ++q)
+                if (2 * q < nsl)
+                  reinterpret_cast<double2*>(row)[q] =
+                      make_double2(vslot(Ftw, blk * 32 + 2 * q), vslot(Ftw, blk * 32 + 2 * q + 1));
+            }
+          }
+          __syncwarp();
+          R sF = R(0), sT = R(0);
+          if constexpr (TWO && sizeof(R) == 4) {
+            float2 acc = make_float2(0.f, 0.f);
+  #pragma unroll
+            for (int L = 0; L < NP; ++L) acc = __fadd2_rn(acc, reinterpret_cast<const float2*>(trows + L * TS)[lg]);
+            sF = acc.x;
+            sT = acc.y;
+          } else if constexpr (TWO) {
+  #pragma unroll
+            for (int L = 0; L < NP; ++L) {
+              const double2 x = reinterpret_cast<const double2*>(trows + L * TS)[lg];
+              sF += x.x;
+              sT += x.y;
+            }
+          } else {
+  #pragma unroll
+            for (int L = 0; L < NP; ++L) sT += trows[L * TS + lg];
+          }
+          __syncwarp();  // the rows are rewritten by the next block
+          // one finish per lane and pass: output blk 32 + lg of the pass, else
+          // (last pass) mode-0 output lg - RM
+          int jo = blk * 32 + lg;
+          int v = jo / (NM - 1), n = 1 + jo % (NM - 1);
+          bool act = jo < NV;
+          if (!act && blk == NBLK - 1 && M0_LAST && lg < RM + 5) {
+            v = lg - RM;
+            n = 0;
+            sF = sT = R(0);
+            act = true;
+          }
+          if (act && live) finish(v, n, i0 + cb, cb, sF, sT);
+        }
+        if constexpr (!M0_LAST) {
+          if (lg >= 32 - 5 && live) finish(lg - (32 - 5), 0, i0 + cb, cb, R(0), R(0));
+        }
+      } else {
+      // ---- several cells per warp (n_q = 2): the PG lanes of a cell reduce
+      // PG volume outputs (modes n >= 1, j = v (NM-1) + n-1) at a time by a
+      // butterfly, after which lane lg holds output j = blk PG + lg of both
+      // kinds (F and F_t) and finishes it.  When the last block of RM outputs
+      // fits twice into PG slots, its F and F_t sums share one butterfly (F in
+      // slots 0..RM-1, F_t in RM..2RM-1) and a shuffle pairs them.  The five
+      // mode-0 outputs have face terms only. ----
+      constexpr int NB = NV / PG, RM = NV % PG;
+      constexpr bool PACK = MODE != MODE_STAGE2 && RM > 0 && 2 * RM <= PG;
+      constexpr int NBLK = NB + ((RM > 0 && !PACK) ? 1 : 0);
+      constexpr bool M0_LAST = RM > 0 && RM + 5 <= PG;  // mode 0 on the idle lanes of the last pass
       // one finish per lane and pass: output j < NV of the pass, else (last
       // pass) mode-0 output lg - RM
       auto finish_pass = [&](int j, bool last, R sF, R sT) {
@@ -734,6 +829,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       }
       if constexpr (!M0_LAST) {
         if (lg >= PG - 5 && live) finish(lg - (PG - 5), 0, i0 + cb, cb, R(0), R(0));
+      }
       }
     } else {
       // ---- a cell spans GW warps: per-warp butterflies over the modes n >= 1,
@@ -777,28 +873,37 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     // the slowest of its warps, not for memory.
     Tin(*raw)[NC][CB] = reinterpret_cast<Tin(*)[NC][CB]>(smem_raw);
     R(*cvt)[CB] = reinterpret_cast<R(*)[CB]>(smem_raw + S::cvt_off);  // converted copy (Tin != R)
-    const int ntx = (nx + CB - 1) / CB;
-    const long long ntiles = (long long)ntx * ny * nz;
-    auto issue = [&](long long t, int b) {
-      const int i0 = (int)(t % ntx) * CB;
-      const long long r = t / ntx;
-      const size_t row = (size_t)r * nx;  // r = k ny + j
+    // tile t = (k ny + j) ntx + tx, coordinates computed once per tile in 32
+    // bits (the host keeps the tile count below 2^31)
+    struct TileAt {
+      int i0, j, k;
+      size_t row;  // (k ny + j) nx
+    };
+    const unsigned ntx = (unsigned)(nx + CB - 1) / CB, ntiles = ntx * (unsigned)ny * (unsigned)nz;
+    auto at = [&](unsigned t) {
+      TileAt a;
+      const unsigned r = t / ntx;
+      a.i0 = (int)(t - r * ntx) * CB;
+      a.j = (int)(r % (unsigned)ny);
+      a.k = (int)(r / (unsigned)ny);
+      a.row = (size_t)r * nx;
+      return a;
+    };
+    auto issue = [&](const TileAt& a, int b) {
       for (int e = tid; e < NC * CB; e += nthr) {
-        const int cc = e % CB, comp = e / CB, i = i0 + cc;
-        cp_async_zfill(&raw[b][comp][cc], Qin + (size_t)comp * nc + row + (i < nx ? i : 0), i < nx);
+        const int cc = e % CB, comp = e / CB, i = a.i0 + cc;
+        cp_async_zfill(&raw[b][comp][cc], Qin + (size_t)comp * nc + a.row + (i < nx ? i : 0), i < nx);
       }
       cp_async_commit();
     };
-    // outputs of tile tt (in so[bb]) -> global memory, a row of CB consecutive
+    // outputs of a tile (in so[bb]) -> global memory, a row of CB consecutive
     // cells per (variable, mode): whole sectors instead of one value per row
     E(*so)[2][NC][CB] = reinterpret_cast<E(*)[2][NC][CB]>(smem_raw + S::out_off);
-    auto flush = [&](long long tt, int bb) {
-      const int i0 = (int)(tt % ntx) * CB;
-      const size_t row = (size_t)(tt / ntx) * nx;
+    auto flush = [&](const TileAt& a, int bb) {
       for (int e = tid; e < NC * CB; e += nthr) {
-        const int cc = e % CB, o = e / CB, i = i0 + cc;
+        const int cc = e % CB, o = e / CB, i = a.i0 + cc;
         if (i >= nx) continue;
-        const size_t idx = (size_t)o * nc + row + i;
+        const size_t idx = (size_t)o * nc + a.row + i;
         if (MODE == MODE_RESIDUAL) {
           io.L[idx] = (double)so[bb][0][o][cc];
           io.Lt[idx] = (double)so[bb][1][o][cc];
@@ -819,10 +924,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     // low faces along x, y, z and the high neighbours'), one tile ahead: they
     // were written by the face kernels long before and are no longer in L2.
     // (Stage 2 reads only their F_t halves, and ran slower with it.)
-    auto prefetch_faces = [&](long long tt) {
-      const int i0 = (int)(tt % ntx) * CB;
-      const long long r = tt / ntx;
-      const int jj = (int)(r % ny), kk = (int)(r / ny);
+    auto prefetch_faces = [&](const TileAt& a) {
       constexpr int LINES = (10 * NT * (int)sizeof(R) + 127) / 128;  // 128-byte lines per face block
       for (int e = tid; e < (5 * CB + 1) * LINES; e += nthr) {
         const int sl = e / LINES, ln = e % LINES;
@@ -834,25 +936,30 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         } else {
           D = 2, s = (sl - 3 * CB - 1) % CB, hi = (sl - 3 * CB - 1) / CB;
         }
-        int i = i0 + s;
+        int i = a.i0 + s;
         if (i >= nx) i -= nx;
         if (i >= nx) continue;
-        const int cj = (D == 1 && hi) ? wrapm(jj + 1, ny) : jj, ck = (D == 2 && hi) ? wrapm(kk + 1, nz) : kk;
+        const int cj = (D == 1 && hi) ? wrapm(a.j + 1, ny) : a.j, ck = (D == 2 && hi) ? wrapm(a.k + 1, nz) : a.k;
         const R* pf = G + ((size_t)D * nc + ((size_t)ck * ny + cj) * nx + i) * (10 * NT) + ln * (128 / sizeof(R));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(pf));
       }
     };
-    long long t = blockIdx.x, tprev = -1;
-    if (t < ntiles) issue(t, 0);
+    unsigned t = blockIdx.x;
+    TileAt cur = at(t), prev = cur;
+    bool have_prev = false;
+    if (t < ntiles) issue(cur, 0);
     int b = 0;
     for (; t < ntiles; t += gridDim.x, b ^= 1) {
       cp_async_wait_all();
       __syncthreads();  // tile t staged by all threads; every warp is done with buffer b ^ 1
-      if (t + gridDim.x < ntiles) {
-        issue(t + gridDim.x, b ^ 1);
-        if (MODE != MODE_STAGE2) prefetch_faces(t + gridDim.x);
+      const unsigned tn = t + gridDim.x;
+      TileAt nxt = cur;
+      if (tn < ntiles) {
+        nxt = at(tn);
+        issue(nxt, b ^ 1);
+        if (MODE != MODE_STAGE2) prefetch_faces(nxt);
       }
-      if (tprev >= 0) flush(tprev, b ^ 1);
+      if (have_prev) flush(prev, b ^ 1);
       const R(*coef)[CB];
       if constexpr (std::is_same<Tin, R>::value) {
         coef = raw[b];
@@ -865,13 +972,13 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         __syncwarp();
         coef = cvt;
       }
-      const int i0 = (int)(t % ntx) * CB;
-      const long long r = t / ntx;
-      tile(i0, (int)(r % ny), (int)(r / ny), coef, so[b]);
-      tprev = t;
+      tile(cur.i0, cur.j, cur.k, coef, so[b]);
+      prev = cur;
+      have_prev = true;
+      cur = nxt;
     }
     __syncthreads();
-    if (tprev >= 0) flush(tprev, b ^ 1);
+    if (have_prev) flush(prev, b ^ 1);
   } else {
     R(*coef)[CB] = reinterpret_cast<R(*)[CB]>(smem_raw + S::cvt_off);
     const int i0 = blockIdx.x * CB, j = blockIdx.y, k = blockIdx.z;
@@ -892,7 +999,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
 template <class R, int ORDER, int NQ, int MODE, class Tin, class E = R>
 inline void cell_launch_config(const MeshDev& m, dim3& grid, size_t& smem) {
   using LY = CellLayout<ORDER, NQ>;
-  smem = CellSmem<R, ORDER, NQ, Tin, E>::bytes;
+  smem = CellSmem<R, ORDER, NQ, Tin, E, MODE>::bytes;
   const long long ntx = (m.nx + LY::CB - 1) / LY::CB;
   if (LY::GW != 1) {
     grid = dim3((unsigned)ntx, (unsigned)m.ny, (unsigned)m.nz);

@@ -179,10 +179,10 @@ struct Impl {
     DG_ATTR((k_face<R, ORDER, NQ, 0, R, true>), FS::bytes)
     DG_ATTR((k_face<R, ORDER, NQ, 1, R, true>), FS::bytes)
     DG_ATTR((k_face<R, ORDER, NQ, 2, R, true>), FS::bytes)
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_RESIDUAL, double, E>), (CellSmem<R, ORDER, NQ, double, E>::bytes))
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, double, E>), (CellSmem<R, ORDER, NQ, double, E>::bytes))
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, R, E>), (CellSmem<R, ORDER, NQ, R, E>::bytes))
-    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE2, R, E>), (CellSmem<R, ORDER, NQ, R, E>::bytes))
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_RESIDUAL, double, E>), (CellSmem<R, ORDER, NQ, double, E, MODE_RESIDUAL>::bytes))
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, double, E>), (CellSmem<R, ORDER, NQ, double, E, MODE_STAGE1>::bytes))
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE1, R, E>), (CellSmem<R, ORDER, NQ, R, E, MODE_STAGE1>::bytes))
+    DG_ATTR((k_cell<R, ORDER, NQ, MODE_STAGE2, R, E>), (CellSmem<R, ORDER, NQ, R, E, MODE_STAGE2>::bytes))
 #undef DG_ATTR
     return e;
   }
@@ -387,6 +387,9 @@ int dghgks_init(const dghgks_mesh* mesh, int order, double gamma, double mu, dou
   if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || mesh->ny > 65535 || mesh->nz > 65535)
     return fail(nullptr, DGHGKS_EARG, "bad mesh size %d x %d x %d", mesh->nx, mesh->ny, mesh->nz);
   const int n3[3] = {mesh->nx, mesh->ny, mesh->nz};
+  // the cell kernels number their tiles of 8 cells in 32 bits
+  if ((long long)((mesh->nx + 7) / 8) * mesh->ny * mesh->nz >= (1LL << 31))
+    return fail(nullptr, DGHGKS_EUNSUP, "mesh of %d x %d x %d cells: too many cell tiles", mesh->nx, mesh->ny, mesh->nz);
   bool nonuniform = false;
   for (int d = 0; d < 3; ++d) {
     if (mesh->nodes[d]) {
