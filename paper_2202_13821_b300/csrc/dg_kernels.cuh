@@ -445,7 +445,10 @@ struct CellSmem {
   static constexpr bool TRANS = LY::GW == 1 && LY::PG == 32;
   static constexpr int TS = (MODE == MODE_STAGE2 ? 32 : 64) + 16 / (int)sizeof(R);
   static constexpr size_t tr = TRANS ? sizeof(R) * LY::WARPS * LY::NP * TS : 0;
-  static constexpr size_t tabs = sizeof(E) * NM + sizeof(int) * 6 * NM;
+  // per output (v, n): its offsets v NT + t_D(n) in the face blocks normal to
+  // D = 0, 1, 2 and the parity signs (-1)^{n_D}; M^-1 per mode; per mode the
+  // tangential indices and signs again as ints (cells spanning two warps)
+  static constexpr size_t tabs = 16 * NC + sizeof(E) * 4 * NC + sizeof(E) * NM + sizeof(int) * 6 * NM;
   static constexpr size_t cvt_off = raw, red_off = raw + cvt, out_off = raw + cvt + red, tr_off = out_off + out,
                           tab_off = tr_off + tr;
   static constexpr size_t bytes = raw + cvt + red + out + tr + tabs;
@@ -540,7 +543,9 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
   constexpr int NOUT = LY::NOUT, NOP = LY::NOP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R(*red)[GW][2][NOP] = reinterpret_cast<R(*)[GW][2][NOP]>(smem_raw + S::red_off);  // GW > 1 only
-  E* invM = reinterpret_cast<E*>(smem_raw + S::tab_off);
+  int4* dsc = reinterpret_cast<int4*>(smem_raw + S::tab_off);  // [NC] face-block offsets of output v NM + n
+  E(*dsg)[4] = reinterpret_cast<E(*)[4]>(dsc + NC);            // [NC] their parity signs
+  E* invM = reinterpret_cast<E*>(dsg + NC);
   int* tix = reinterpret_cast<int*>(invM + NM);  // [3][NM] tangential index, then [3][NM] parity sign
   const int tid = threadIdx.x, nthr = LY::WARPS * 32;
   const int lane = tid & 31, lg = lane % PG, warp = tid >> 5;
@@ -560,6 +565,17 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       tix[D * NM + e] = tmode_index(mode_exp(e, tan1(D)), mode_exp(e, tan2(D)));
       tix[3 * NM + D * NM + e] = (mode_exp(e, D) % 2 == 0) ? 1 : -1;
     }
+  }
+  for (int e = tid; e < NC; e += nthr) {
+    const int v = e / NM, n = e % NM;
+    int off[3];
+  #pragma unroll
+    for (int D = 0; D < 3; ++D) {
+      off[D] = v * NT + tmode_index(mode_exp(n, tan1(D)), mode_exp(n, tan2(D)));
+      dsg[e][D] = (mode_exp(n, D) % 2 == 0) ? E(1) : E(-1);
+    }
+    dsc[e] = make_int4(off[0], off[1], off[2], n);
+    dsg[e][3] = E(0);
   }
 
   const E h = (E)dt, h2 = (E)(dt * dt);
@@ -620,6 +636,22 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         }
     }
 
+    // One cell per warp: the face-moment blocks of this lane's cell, its low
+    // faces normal to D = 0, 1, 2 (fb[D]) and its high neighbours' (fb[3 + D]),
+    // addressed once per tile.
+    const R* fb[6];
+    if constexpr (GW == 1) {
+      const int ic = i0 + cb < nx ? i0 + cb : nx - 1;
+      const size_t cell = row + ic;
+      const size_t up[3] = {row + wrapm(ic + 1, nx), ((size_t)k * ny + wrapm(j + 1, ny)) * nx + ic,
+                            ((size_t)wrapm(k + 1, nz) * ny + j) * nx + ic};
+  #pragma unroll
+      for (int D = 0; D < 3; ++D) {
+        fb[D] = G + ((size_t)D * nc + cell) * (10 * NT);
+        fb[3 + D] = G + ((size_t)D * nc + up[D]) * (10 * NT);
+      }
+    }
+
     // One output (variable v, mode n) of the cell at x index i: the six faces'
     // moments with the sign/parity of Eq. (operator), M^-1, and the stage
     // epilogue in the precision E; with E = R the accumulation into the
@@ -628,6 +660,26 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       E sF = (E)sF_, sT = (E)sT_;
       const size_t cell = row + i;
       const size_t idx = (size_t)(v * NM + n) * nc + cell;
+      if constexpr (GW == 1) {
+        const int o = v * NM + n;
+        const int4 ds = dsc[o];
+        const int dof[3] = {ds.x, ds.y, ds.z};
+        E sg[3];
+        if constexpr (sizeof(E) == 4) {
+          const float4 q = *reinterpret_cast<const float4*>(dsg[o]);
+          sg[0] = q.x, sg[1] = q.y, sg[2] = q.z;
+        } else {
+          const double2 q0 = reinterpret_cast<const double2*>(dsg[o])[0];
+          sg[0] = q0.x, sg[1] = q0.y, sg[2] = dsg[o][2];
+        }
+  #pragma unroll
+        for (int D = 0; D < 3; ++D) {
+          const R* lo = fb[D] + dof[D];
+          const R* hi = fb[3 + D] + dof[D];
+          sF += sg[D] * (E)lo[0] - (E)hi[0];
+          sT += sg[D] * (E)lo[5 * NT] - (E)hi[5 * NT];
+        }
+      } else {
   #pragma unroll
       for (int D = 0; D < 3; ++D) {
         const int t = tix[D * NM + n];
@@ -642,6 +694,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         const R* gD = G + (size_t)D * nc * (10 * NT) + v * NT + t;  // face-major: [D][face][10][NT]
         sF += sg * (E)gD[cell * (10 * NT)] - (E)gD[up * (10 * NT)];
         sT += sg * (E)gD[cell * (10 * NT) + 5 * NT] - (E)gD[up * (10 * NT) + 5 * NT];
+      }
       }
       E iM = invM[n];
       if (mesh_nonuniform(m))  // 1/|K| = (2/h_x)(2/h_y)(2/h_z) / 8
@@ -744,23 +797,49 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
             }
           }
           __syncwarp();
+          // NQ partial sums, one per plane of points (the rows L = a NQ^2 + ...
+          // of one a), then combined in order: NQ independent add chains
           R sF = R(0), sT = R(0);
           if constexpr (TWO && sizeof(R) == 4) {
-            float2 acc = make_float2(0.f, 0.f);
+            float2 acc[NQ];
   #pragma unroll
-            for (int L = 0; L < NP; ++L) acc = __fadd2_rn(acc, reinterpret_cast<const float2*>(trows + L * TS)[lg]);
-            sF = acc.x;
-            sT = acc.y;
+            for (int a = 0; a < NQ; ++a) {
+              acc[a] = reinterpret_cast<const float2*>(trows + a * NQ * NQ * TS)[lg];
+  #pragma unroll
+              for (int L = a * NQ * NQ + 1; L < (a + 1) * NQ * NQ; ++L)
+                acc[a] = __fadd2_rn(acc[a], reinterpret_cast<const float2*>(trows + L * TS)[lg]);
+            }
+  #pragma unroll
+            for (int a = 1; a < NQ; ++a) acc[0] = __fadd2_rn(acc[0], acc[a]);
+            sF = acc[0].x;
+            sT = acc[0].y;
           } else if constexpr (TWO) {
+            R aF[NQ], aT[NQ];
   #pragma unroll
-            for (int L = 0; L < NP; ++L) {
-              const double2 x = reinterpret_cast<const double2*>(trows + L * TS)[lg];
-              sF += x.x;
-              sT += x.y;
+            for (int a = 0; a < NQ; ++a) {
+              aF[a] = aT[a] = R(0);
+  #pragma unroll
+              for (int L = a * NQ * NQ; L < (a + 1) * NQ * NQ; ++L) {
+                const double2 x = reinterpret_cast<const double2*>(trows + L * TS)[lg];
+                aF[a] += x.x;
+                aT[a] += x.y;
+              }
+            }
+  #pragma unroll
+            for (int a = 0; a < NQ; ++a) {
+              sF += aF[a];
+              sT += aT[a];
             }
           } else {
+            R aT[NQ];
   #pragma unroll
-            for (int L = 0; L < NP; ++L) sT += trows[L * TS + lg];
+            for (int a = 0; a < NQ; ++a) {
+              aT[a] = trows[a * NQ * NQ * TS + lg];
+  #pragma unroll
+              for (int L = a * NQ * NQ + 1; L < (a + 1) * NQ * NQ; ++L) aT[a] += trows[L * TS + lg];
+            }
+  #pragma unroll
+            for (int a = 0; a < NQ; ++a) sT = a ? sT + aT[a] : aT[0];
           }
           __syncwarp();  // the rows are rewritten by the next block
           // one finish per lane and pass: output blk 32 + lg of the pass, else
