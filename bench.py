@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--ref-n", type=int, default=16, help="grid of the reference arm's oracle steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stage64", action="store_true", help="skip the FP32-flux / FP64-stage leg")
+    ap.add_argument("--cpu-config2", action="store_true",
+                    help="also time the oracle on BASELINE configuration 2 in full (64^3 P2, 2 steps; ~2 min)")
     ap.add_argument("--adjoint-n", type=int, default=64, help="cells per direction of the adjoint leg (0: skip)")
     ap.add_argument("--adjoint-steps", type=int, default=100, help="checkpointed steps of the adjoint leg")
     return ap.parse_args()
@@ -191,6 +193,24 @@ def oracle_config1():
     oracle.step(pb, Q, dt, ns)
     el = time.perf_counter() - t0
     return 8 ** 3 * 5 * 4 * 2 * ns / el, el, ns
+
+
+def oracle_config2(nsteps=2):
+    """BASELINE configuration 2 run by the oracle: Taylor-Green 64^3 P2, n_q = 3, dt from CFL 0.15, nsteps
+    S2O4 steps from the projected initial state.  Returns (DOF-stage-updates/s, seconds)."""
+    import oracle
+    from paper_2202_13821_b300 import inputs
+
+    oracle.build()
+    n = 64
+    dt = inputs.tgv_dt(n, ORDER)
+    pb = oracle.Problem(order=ORDER, nq=NQ, n=(n, n, n), lo=(-math.pi,) * 3, hi=(math.pi,) * 3, mu=MU, Pr=PR,
+                        gamma=GAMMA)
+    Q = inputs.tgv_state(n, ORDER, device="cpu").numpy()
+    t0 = time.perf_counter()
+    oracle.step(pb, Q, dt, nsteps)
+    el = time.perf_counter() - t0
+    return n ** 3 * 50 * 2 * nsteps / el, el
 
 
 def run_reference(args):
@@ -625,6 +645,10 @@ def run_ours(args):
                          f"2 steps / time",
                "config1_full_run": {"value": cfg1_rate, "seconds": cfg1_s, "steps": cfg1_steps,
                                     "workload": "3D density advection 8^3 P1, n_q = 2, S2O4 to t = 0.1"}}
+        if args.cpu_config2:
+            c2_rate, c2_s = oracle_config2()
+            cpu["config2_full_run"] = {"value": c2_rate, "seconds": c2_s, "steps": 2,
+                                       "workload": "Taylor-Green 64^3 P2, n_q = 3, dt from CFL 0.15, 2 S2O4 steps"}
         # error of each GPU path against the oracle at the box centres after 2 steps (the 9^3 box holds every
         # cell a centre depends on after 4 stages, so the oracle's centre values are those of the full grid)
         Q0c = torch.stack([Q0[:, :, k, j, i] for (i, j, k) in cells]).cpu().numpy()
