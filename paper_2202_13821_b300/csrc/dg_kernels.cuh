@@ -566,7 +566,9 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       tix[3 * NM + D * NM + e] = (mode_exp(e, D) % 2 == 0) ? 1 : -1;
     }
   }
-  for (int e = tid; e < NC; e += nthr) {
+  // (the descriptors serve the persistent one-cell-per-warp layout only; at
+  // n_q = 4 every CTA handles one tile and would rebuild them for nothing)
+  for (int e = tid; GW == 1 && e < NC; e += nthr) {
     const int v = e / NM, n = e % NM;
     int off[3];
   #pragma unroll
