@@ -333,27 +333,31 @@ def test_fp32_mixed_error_128_cubed(torch, api):
         assert l2 < 0.5 * change
 
 
-@pytest.mark.parametrize("precision,nsteps", [(1, 400), (0, 300)])
-def test_prandtl_072_long_run_stays_bounded(torch, api, precision, nsteps):
-    """Taylor-Green 64^3 P2 at Pr = 0.72 over hundreds of steps: the P2 modes must stay at the size of
-    the resolved flow.  With the Prandtl correction also applied to the fitted time derivative F_t
+@pytest.mark.parametrize("order,nq,precision,nsteps", [(2, 3, 1, 400), (2, 3, 0, 300), (1, 2, 1, 400),
+                                                   (3, 3, 1, 300), (3, 4, 1, 300), (2, 3, 2, 400)])
+def test_prandtl_072_long_run_stays_bounded(torch, api, order, nq, precision, nsteps):
+    """Taylor-Green at Pr = 0.72 over hundreds of steps, every cell-kernel layout (P1 n_q = 2, P2 n_q = 3,
+    P3 n_q = 3 and 4) and all three precisions for P2: the highest modes must stay at the size of the
+    resolved flow.  With the Prandtl correction also applied to the fitted time derivative F_t
     (a reading since dropped: the heat flux about the velocity of t_n, differentiated in time,
     carries a frame-shift term in d_t U) both precisions doubled their largest P2 coefficient every
     ~20 steps from step ~60 and failed with non-physical states before step 300; with the correction
     on F only the largest P2 coefficient grows by 10 % over 400 steps, as with Pr = 1."""
     from paper_2202_13821_b300 import inputs
 
-    n = 64
-    dt = inputs.tgv_dt(n, 2)
-    s = api.Solver((n,) * 3, **TGV, order=2, mu=1 / 1600, Pr=0.72, n_q=3, precision=precision)
-    Q = inputs.tgv_state(n, 2, device="cuda")
+    n = 64 if order < 3 else 48
+    dt = inputs.tgv_dt(n, order, cfl=0.09 if order == 3 else 0.15)  # the paper's CFL numbers (Sec. 5.3)
+    s = api.Solver((n,) * 3, **TGV, order=order, mu=1 / 1600, Pr=0.72, n_q=nq, precision=precision)
+    Q = inputs.tgv_state(n, order, device="cuda")
+    hi = slice(1, None) if order == 1 else slice(4, None)  # the highest-degree modes present
     s.steps(Q, dt, 50)
-    a50 = float(Q[:, 4:].abs().max())
+    a50 = float(Q[:, hi].abs().max())
     s.steps(Q, dt, nsteps - 50)
     s.status()
     assert bool(torch.isfinite(Q).all())
-    a_end = float(Q[:, 4:].abs().max())
-    print(f"precision {precision}: largest P2 coefficient {a50:.3e} after 50 steps, {a_end:.3e} after {nsteps}")
+    a_end = float(Q[:, hi].abs().max())
+    print(f"P{order} n_q={nq} precision {precision}: largest high-mode coefficient {a50:.3e} after 50 steps, "
+          f"{a_end:.3e} after {nsteps}")
     assert a_end < 1.5 * a50
 
 
