@@ -18,11 +18,15 @@
 //     face); point values never do.
 //
 //   k_cell<MODE>: a group of lanes owns one cell, one lane per Gauss point
-//     (a warp per cell at n_q = 3, four cells per warp at n_q = 2).  Each lane
-//     evaluates the interior flux of Eq. (flux-2) at its point; the volume
-//     projection w |K| F . grad B_n is summed over the group by a
-//     recursive-halving warp butterfly (deterministic, no shared-memory
-//     projection, no atomics).  The CTA then adds the six faces' moments with
+//     (a warp per cell at n_q = 3, four cells per warp at n_q = 2, two warps
+//     per cell at n_q = 4).  Each lane evaluates Q_h and grad Q_h at its point
+//     (cell-major coefficient rows and, at k <= 2, a per-CTA table of the
+//     basis at the points, both read with 16-byte loads) and the interior
+//     flux of Eq. (flux-2) there; the volume projection w |K| F . grad B_n is
+//     summed over the cell's lanes in a fixed order (one cell per warp:
+//     transposed through shared memory, each lane summing one output column;
+//     otherwise by recursive-halving warp butterflies; no atomics).  The
+//     cell's lanes then add the six faces' moments with
 //     the sign and parity of Eq. (operator) (the cell is right of its low
 //     face: +(-1)^{n_D} G, left of its high face: -G), multiplies by the
 //     diagonal inverse mass matrix, and applies the epilogue:
@@ -33,8 +37,7 @@
 //     path) stores Q* and inc in the flux precision, and the accumulation into
 //     the stored FP64 state is the one FP64 operation (on B300 an FP64
 //     instruction costs ~64 FP32 ones).  E = double with R = float (the
-//     FP32-flux / FP64-stage path): the volume sums leave the butterflies in
-//     FP32, and the assembly with the face moments, M^-1, Q* and inc are FP64
+//     FP32-flux / FP64-stage path): the volume sums are FP32, and the assembly with the face moments, M^-1, Q* and inc are FP64
 //     (Q* formed from the FP64 state and stored rounded to R, its precision
 //     as an input of the stage-2 flux kernels; inc stored in FP64).
 //
@@ -423,20 +426,69 @@ struct CellLayout {
   static_assert(NP <= 64, "k_cell handles up to 4^3 points per cell");
 };
 
+// Basis of k_cell at a Gauss point p: the values phi_n(p), the gradients
+// d phi_n / d r_d (p) and the weight product w_a w_b w_c, as products of the
+// Legendre values at the Gauss nodes in the flux precision.  The persistent
+// one-warp-per-cell layout at k <= 2 keeps them in shared memory, one row per
+// point (built once per CTA; a lane loads its row with 16-byte loads):
+//   [0, POFF): the gradients of the pairs (n, d) with a non-zero exponent
+//     along d, at slot d NGD + (index of the mode with that exponent lowered
+//     by one; NGD = modes of degree k - 1),
+//   [POFF, WOFF): phi_n,  WOFF: the weight,
+// each section padded to a multiple of 4 values.  Otherwise (k = 3, whose
+// row would crowd the registers, or a cell over two warps) a lane forms them
+// from the Legendre values held in registers.
+template <class R, int ORDER, int NQ>
+struct CellBasis {
+  static constexpr int NM = n_modes(ORDER), NGD = n_modes(ORDER - 1);
+  static constexpr int POFF = (3 * NGD + 3) / 4 * 4, WOFF = POFF + (NM + 3) / 4 * 4, BW = WOFF + 4;
+  static constexpr int gslot(int n, int d) {
+    return d * NGD + mode_index2(mode_exp(n, 0) - (d == 0), mode_exp(n, 1) - (d == 1), mode_exp(n, 2) - (d == 2));
+  }
+  R L[3][ORDER + 1], dL[3][ORDER + 1], w;
+  __device__ __forceinline__ explicit CellBasis(int p) {
+    const int pa[3] = {p / (NQ * NQ), (p / NQ) % NQ, p % NQ};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const R x = gauss_xr<R>(NQ, pa[d]);
+#pragma unroll
+      for (int n = 0; n <= ORDER; ++n) {
+        L[d][n] = leg<R>(n, x);
+        dL[d][n] = dleg<R>(n, x);
+      }
+    }
+    w = gauss_wr<R>(NQ, pa[0]) * gauss_wr<R>(NQ, pa[1]) * gauss_wr<R>(NQ, pa[2]);
+  }
+  // (mm, d compile-time after unrolling)
+  __device__ __forceinline__ R phi(int mm) const {
+    return L[0][mode_exp(mm, 0)] * L[1][mode_exp(mm, 1)] * L[2][mode_exp(mm, 2)];
+  }
+  __device__ __forceinline__ R grad(int mm, int d) const {
+    return (d == 0 ? dL[0][mode_exp(mm, 0)] : L[0][mode_exp(mm, 0)]) *
+           (d == 1 ? dL[1][mode_exp(mm, 1)] : L[1][mode_exp(mm, 1)]) *
+           (d == 2 ? dL[2][mode_exp(mm, 2)] : L[2][mode_exp(mm, 2)]);
+  }
+};
+
 template <class R, int ORDER, int NQ, class Tin = R, class E = R, int MODE = MODE_RESIDUAL>
 struct CellSmem {
   using LY = CellLayout<ORDER, NQ>;
   static constexpr int NM = LY::NM, NC = 5 * NM, CB = LY::CB;
+  // the coefficients of a tile are staged cell-major: per cell a row of the
+  // 5 variables' NM modes, each variable padded to NMP values (v NMP + n), so
+  // that a lane reads a variable's modes with 16-byte loads
+  static constexpr int NMP = (NM + 3) / 4 * 4, NCP = 5 * NMP;
   // GW = 1: two staging buffers of the input type (cp.async targets), plus a
   // converted copy when the input is not in the flux precision; GW > 1: one
   // buffer in the flux precision.
-  static constexpr size_t raw = LY::GW == 1 ? 2 * sizeof(Tin) * NC * CB : 0;
-  static constexpr size_t cvt = (LY::GW == 1 && std::is_same<Tin, R>::value) ? 0 : sizeof(R) * NC * CB;
+  static constexpr size_t raw = LY::GW == 1 ? 2 * sizeof(Tin) * NCP * CB : 0;
+  static constexpr size_t cvt = (LY::GW == 1 && std::is_same<Tin, R>::value) ? 0 : sizeof(R) * NCP * CB;
   // cross-warp partial sums (only when a cell spans two warps)
   static constexpr size_t red = LY::GW == 1 ? 0 : sizeof(R) * CB * LY::GW * 2 * LY::NOP;
-  // GW = 1: the outputs of a tile (two kinds, NC x CB), double-buffered, so
-  // that they leave as rows of CB consecutive cells
-  static constexpr size_t out = LY::GW == 1 ? sizeof(E) * 2 * 2 * NC * CB : 0;
+  // GW = 1: the outputs of a tile (NKO kinds: two, one at stage 2; NC x CB),
+  // double-buffered, so that they leave as rows of CB consecutive cells
+  static constexpr int NKO = MODE == MODE_STAGE2 ? 1 : 2;
+  static constexpr size_t out = LY::GW == 1 ? sizeof(E) * 2 * NKO * NC * CB : 0;
   // one cell per warp (n_q = 3): the volume projection is transposed through
   // shared memory, a row per Gauss point and warp holding the point's
   // contributions to 32 outputs, (F, F_t) pairs (F_t alone at stage 2); the
@@ -449,10 +501,15 @@ struct CellSmem {
   // D = 0, 1, 2 and the parity signs (-1)^{n_D}; M^-1 per mode; per mode the
   // tangential indices and signs again as ints (cells spanning two warps)
   static constexpr size_t tabs = 16 * NC + sizeof(E) * 4 * NC + sizeof(E) * NM + sizeof(int) * 6 * NM;
-  static constexpr size_t cvt_off = raw, red_off = raw + cvt, out_off = raw + cvt + red, tr_off = out_off + out,
-                          tab_off = tr_off + tr;
-  static constexpr size_t bytes = raw + cvt + red + out + tr + tabs;
+  // the basis table (CellBasis), one row per Gauss point (persistent layout, k <= 2)
+  static constexpr bool TABLE = LY::GW == 1 && ORDER <= 2;
+  static constexpr size_t bt = TABLE ? sizeof(R) * LY::NP * CellBasis<R, ORDER, NQ>::BW : 0;
+  static constexpr size_t cvt_off = raw, red_off = raw + cvt, out_off = red_off + red, tr_off = out_off + out,
+                          bt_off = tr_off + tr, tab_off = bt_off + bt;
+  static constexpr size_t bytes = tab_off + tabs;
+  static_assert(cvt_off % 16 == 0 && red_off % 16 == 0 && out_off % 16 == 0, "16-byte aligned staging");
   static_assert(tr_off % 16 == 0 && tr % 16 == 0, "16-byte aligned transpose rows");
+  static_assert(bt_off % 16 == 0 && tab_off % 16 == 0, "16-byte aligned basis rows and tables");
 };
 
 // Recursive-halving butterfly over the PG lanes of a group: in[N] per lane ->
@@ -540,8 +597,10 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
   using S = CellSmem<R, ORDER, NQ, Tin, E, MODE>;
   constexpr bool SPLIT = !std::is_same<E, R>::value;  // FP32 flux, FP64 epilogue
   constexpr int NM = LY::NM, NP = LY::NP, NC = S::NC, CB = LY::CB, PG = LY::PG, GW = LY::GW, NT = n_tmodes(ORDER);
-  constexpr int NOUT = LY::NOUT, NOP = LY::NOP;
+  constexpr int NOUT = LY::NOUT, NOP = LY::NOP, NMP = S::NMP, NCP = S::NCP;
+  using CBs = CellBasis<R, ORDER, NQ>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* const bt = reinterpret_cast<R*>(smem_raw + S::bt_off);  // [NP][BW] basis table
   R(*red)[GW][2][NOP] = reinterpret_cast<R(*)[GW][2][NOP]>(smem_raw + S::red_off);  // GW > 1 only
   int4* dsc = reinterpret_cast<int4*>(smem_raw + S::tab_off);  // [NC] face-block offsets of output v NM + n
   E(*dsg)[4] = reinterpret_cast<E(*)[4]>(dsc + NC);            // [NC] their parity signs
@@ -579,45 +638,71 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     dsc[e] = make_int4(off[0], off[1], off[2], n);
     dsg[e][3] = E(0);
   }
+  // basis table (persistent layout, k <= 2): one row per point
+  for (int p = tid; S::TABLE && p < NP; p += nthr) {
+    const CBs cbas(p);
+    R* const rw = bt + p * CBs::BW;
+  #pragma unroll
+    for (int mm = 0; mm < NM; ++mm) {
+      rw[CBs::POFF + mm] = cbas.phi(mm);
+  #pragma unroll
+      for (int d = 0; d < 3; ++d)
+        if (mode_exp(mm, d) > 0) rw[CBs::gslot(mm, d)] = cbas.grad(mm, d);
+    }
+    rw[CBs::WOFF] = cbas.w;
+  }
 
   const E h = (E)dt, h2 = (E)(dt * dt);
   // Everything after the staging of one tile (CB consecutive cells along x of
   // row (j, k)), reading the coefficients from coef[NC][CB].  With GW = 1 the
   // results go to so[kind][NC][CB] in shared memory (written out by flush).
-  auto tile = [&](const int i0, const int j, const int k, const R (*coef)[CB], E (*so)[NC][CB]) {
+  auto tile = [&](const int i0, const int j, const int k, const R (*coef)[NCP], E (*so)[NC][CB]) {
     const size_t row = ((size_t)k * ny + j) * nx;
     // ---- interior flux of Eq. (flux-2) at this lane's Gauss point ----
+    // Every lane evaluates a physical state: spare lanes take point 0 and
+    // cells beyond the row end hold a copy of a cell of the row (staged so),
+    // so the flux is finite everywhere and a zero weight removes what is not
+    // this cell's.
     const bool active = (pidx < NP) && (i0 + cb < nx);
-    const int pp = active ? pidx : 0;
-    const int pa[3] = {pp / (NQ * NQ), (pp / NQ) % NQ, pp % NQ};
-    R L1[3][ORDER + 1], dL1[3][ORDER + 1];
-  #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const R x = gauss_xr<R>(NQ, pa[d]);
-  #pragma unroll
-      for (int n = 0; n <= ORDER; ++n) {
-        L1[d][n] = leg<R>(n, x);
-        dL1[d][n] = dleg<R>(n, x);
-      }
-    }
+    const int pp = pidx < NP ? pidx : 0;
+    const R* const brow = bt + pp * CBs::BW;  // this point's basis row (table layout)
+    const CBs lbas(pp);                       // the basis in registers otherwise
     const int icell = (i0 + cb < nx) ? i0 + cb : nx - 1;
     const R sc[3] = {cell_sc<R>(m, 0, icell), cell_sc<R>(m, 1, j), cell_sc<R>(m, 2, k)};
     const R cvol = mesh_nonuniform(m) ? cell_w<R>(m, 0, icell) * cell_w<R>(m, 1, j) * cell_w<R>(m, 2, k) : mesh_vol<R>(m);
     R Fw[3][5], Ftw[3][5];  // w |K| (2/h_d) F_d, same for F_t
     {
+      // Q_h and its reference gradients at the point (each variable's
+      // coefficients read four modes at a time with 16-byte loads)
+      R br[S::TABLE ? CBs::WOFF : 4];
+      if constexpr (S::TABLE) lds16<CBs::WOFF>(brow, br);
+      auto phi = [&](int mm) {
+        if constexpr (S::TABLE) return br[CBs::POFF + mm];
+        else return lbas.phi(mm);
+      };
+      auto gph = [&](int mm, int d) {
+        if constexpr (S::TABLE) return br[CBs::gslot(mm, d)];
+        else return lbas.grad(mm, d);
+      };
       R q[5], dq[3][5];
   #pragma unroll
       for (int v = 0; v < 5; ++v) {
         R s0 = R(0), g0 = R(0), g1 = R(0), g2 = R(0);
   #pragma unroll
-        for (int mm = 0; mm < NM; ++mm) {
-          const int e0 = mode_exp(mm, 0), e1 = mode_exp(mm, 1), e2 = mode_exp(mm, 2);
-          const R cv = coef[v * NM + mm][cb];
-          s0 += cv * (L1[0][e0] * L1[1][e1] * L1[2][e2]);
-          // P'_0 = 0: modes constant along an axis have no gradient term there
-          if (e0 > 0) g0 += cv * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
-          if (e1 > 0) g1 += cv * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
-          if (e2 > 0) g2 += cv * (L1[0][e0] * L1[1][e1] * dL1[2][e2]);
+        for (int c0 = 0; c0 < NM; c0 += 4) {
+          R cv[4];
+          lds16<4>(&coef[cb][v * NMP + c0], cv);
+  #pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int mm = c0 + u;
+            if (mm < NM) {
+              s0 += cv[u] * phi(mm);
+              // P'_0 = 0: modes constant along an axis have no gradient term there
+              if (mode_exp(mm, 0) > 0) g0 += cv[u] * gph(mm, 0);
+              if (mode_exp(mm, 1) > 0) g1 += cv[u] * gph(mm, 1);
+              if (mode_exp(mm, 2) > 0) g2 += cv[u] * gph(mm, 2);
+            }
+          }
         }
         q[v] = s0;
         dq[0][v] = g0 * sc[0];
@@ -625,16 +710,15 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         dq[2][v] = g2 * sc[2];
       }
       R F[3][5], Ft[3][5];
-      bool ok = true;
-      if (active) ok = interior_flux(q, dq, gp, F, Ft);
+      const bool ok = interior_flux(q, dq, gp, F, Ft);
       if (active && !ok) atomicOr(flag, 1u);
-      const R w = active ? gauss_wr<R>(NQ, pa[0]) * gauss_wr<R>(NQ, pa[1]) * gauss_wr<R>(NQ, pa[2]) * cvol : R(0);
+      const R w = active ? (S::TABLE ? brow[CBs::WOFF] : lbas.w) * cvol : R(0);
   #pragma unroll
       for (int d = 0; d < 3; ++d)
   #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          Fw[d][v] = active ? w * sc[d] * F[d][v] : R(0);
-          Ftw[d][v] = active ? w * sc[d] * Ft[d][v] : R(0);
+          Fw[d][v] = w * sc[d] * F[d][v];
+          Ftw[d][v] = w * sc[d] * Ft[d][v];
         }
     }
 
@@ -711,7 +795,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
           if constexpr (SPLIT)  // the increment of Q* only; flush adds it to the FP64 state
             so[0][o][cc] = E(0.5) * h * Lv + (h2 * E(0.125)) * Ltv;
           else
-            so[0][o][cc] = coef[o][cc] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
+            so[0][o][cc] = coef[cc][v * NMP + n] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
           so[1][o][cc] = h * Lv + (h2 * E(1.0 / 6.0)) * Ltv;
         } else {
           so[0][o][cc] = Ltv;
@@ -723,7 +807,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         if constexpr (SPLIT)
           io.Qs[idx] = (R)(io.Qn[idx] + (E(0.5) * h * Lv + (h2 * E(0.125)) * Ltv));
         else
-          io.Qs[idx] = coef[v * NM + n][cc] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
+          io.Qs[idx] = coef[cc][v * NMP + n] + (R(0.5) * h * Lv + (h2 * R(0.125)) * Ltv);
         io.inc[idx] = h * Lv + (h2 * E(1.0 / 6.0)) * Ltv;
       } else {
         const double q = io.Qn[idx] + (double)(io.inc[idx] + (h2 * E(1.0 / 3.0)) * Ltv);
@@ -731,15 +815,21 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         if (io.Qf) io.Qf[idx] = (R)q;
       }
     };
-    // this lane's contribution to output o (v = o / NM, mode n = o % NM; mode 0 has no volume term)
+    // this lane's contribution to output o (v = o / NM, mode n = o % NM; mode
+    // 0 has no volume term), with the basis gradients at its point
+    R gr[S::TABLE ? CBs::POFF : 4];
+    if constexpr (S::TABLE) lds16<CBs::POFF>(brow, gr);
+    auto gvol = [&](int n, int d) {
+      if constexpr (S::TABLE) return gr[CBs::gslot(n, d)];
+      else return lbas.grad(n, d);
+    };
     auto vol_term = [&](const R(&Fk)[3][5], int o) {
       R c = R(0);
       if (o < 5 * NM) {
         const int v = o / NM, n = o % NM;
-        const int e0 = mode_exp(n, 0), e1 = mode_exp(n, 1), e2 = mode_exp(n, 2);
-        if (e0 > 0) c += Fk[0][v] * (dL1[0][e0] * L1[1][e1] * L1[2][e2]);
-        if (e1 > 0) c += Fk[1][v] * (L1[0][e0] * dL1[1][e1] * L1[2][e2]);
-        if (e2 > 0) c += Fk[2][v] * (L1[0][e0] * L1[1][e1] * dL1[2][e2]);
+        if (mode_exp(n, 0) > 0) c += Fk[0][v] * gvol(n, 0);
+        if (mode_exp(n, 1) > 0) c += Fk[1][v] * gvol(n, 1);
+        if (mode_exp(n, 2) > 0) c += Fk[2][v] * gvol(n, 2);
       }
       return c;
     };
@@ -952,8 +1042,8 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     // copied global -> shared with cp.async (double buffer) while the current
     // tile is computed, so a CTA waits at its one barrier per tile only for
     // the slowest of its warps, not for memory.
-    Tin(*raw)[NC][CB] = reinterpret_cast<Tin(*)[NC][CB]>(smem_raw);
-    R(*cvt)[CB] = reinterpret_cast<R(*)[CB]>(smem_raw + S::cvt_off);  // converted copy (Tin != R)
+    Tin(*raw)[CB][NCP] = reinterpret_cast<Tin(*)[CB][NCP]>(smem_raw);  // [buffer][cell][v NMP + n]
+    R(*cvt)[NCP] = reinterpret_cast<R(*)[NCP]>(smem_raw + S::cvt_off);  // converted copy (Tin != R)
     // tile t = (k ny + j) ntx + tx, coordinates computed once per tile in 32
     // bits (the host keeps the tile count below 2^31)
     struct TileAt {
@@ -970,30 +1060,33 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       a.row = (size_t)r * nx;
       return a;
     };
+    // (cells beyond the row end get a copy of the row's first cell: every
+    // lane's flux input stays physical)
     auto issue = [&](const TileAt& a, int b) {
       for (int e = tid; e < NC * CB; e += nthr) {
         const int cc = e % CB, comp = e / CB, i = a.i0 + cc;
-        cp_async_zfill(&raw[b][comp][cc], Qin + (size_t)comp * nc + a.row + (i < nx ? i : 0), i < nx);
+        cp_async_zfill(&raw[b][cc][(comp / NM) * NMP + comp % NM], Qin + (size_t)comp * nc + a.row + (i < nx ? i : 0),
+                       true);
       }
       cp_async_commit();
     };
     // outputs of a tile (in so[bb]) -> global memory, a row of CB consecutive
     // cells per (variable, mode): whole sectors instead of one value per row
-    E(*so)[2][NC][CB] = reinterpret_cast<E(*)[2][NC][CB]>(smem_raw + S::out_off);
+    E(*so)[S::NKO][NC][CB] = reinterpret_cast<E(*)[S::NKO][NC][CB]>(smem_raw + S::out_off);
     auto flush = [&](const TileAt& a, int bb) {
       for (int e = tid; e < NC * CB; e += nthr) {
         const int cc = e % CB, o = e / CB, i = a.i0 + cc;
         if (i >= nx) continue;
         const size_t idx = (size_t)o * nc + a.row + i;
-        if (MODE == MODE_RESIDUAL) {
+        if constexpr (MODE == MODE_RESIDUAL) {
           io.L[idx] = (double)so[bb][0][o][cc];
-          io.Lt[idx] = (double)so[bb][1][o][cc];
-        } else if (MODE == MODE_STAGE1) {
+          io.Lt[idx] = (double)so[bb][S::NKO - 1][o][cc];
+        } else if constexpr (MODE == MODE_STAGE1) {
           if constexpr (SPLIT)
             io.Qs[idx] = (R)(io.Qn[idx] + so[bb][0][o][cc]);
           else
             io.Qs[idx] = so[bb][0][o][cc];
-          io.inc[idx] = so[bb][1][o][cc];
+          io.inc[idx] = so[bb][S::NKO - 1][o][cc];
         } else {
           const double q = io.Qn[idx] + (double)(io.inc[idx] + (h2 * E(1.0 / 3.0)) * so[bb][0][o][cc]);
           io.Qn[idx] = q;
@@ -1041,14 +1134,15 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         if (MODE != MODE_STAGE2) prefetch_faces(nxt);
       }
       if (have_prev) flush(prev, b ^ 1);
-      const R(*coef)[CB];
+      const R(*coef)[NCP];
       if constexpr (std::is_same<Tin, R>::value) {
         coef = raw[b];
       } else {
-        // each warp converts its own cells (the only ones it reads)
-        for (int e = lane; e < NC * LY::CPW; e += 32) {
-          const int cc = warp * LY::CPW + e % LY::CPW, comp = e / LY::CPW;
-          cvt[comp][cc] = (R)raw[b][comp][cc];
+        // each warp converts its own cells (the only ones it reads; padding
+        // included, so that the 16-byte loads read defined values)
+        for (int e = lane; e < NCP * LY::CPW; e += 32) {
+          const int cc = warp * LY::CPW + e / NCP, c = e % NCP;
+          cvt[cc][c] = (R)raw[b][cc][c];
         }
         __syncwarp();
         coef = cvt;
@@ -1061,12 +1155,14 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     __syncthreads();
     if (have_prev) flush(prev, b ^ 1);
   } else {
-    R(*coef)[CB] = reinterpret_cast<R(*)[CB]>(smem_raw + S::cvt_off);
+    R(*coef)[NCP] = reinterpret_cast<R(*)[NCP]>(smem_raw + S::cvt_off);
     const int i0 = blockIdx.x * CB, j = blockIdx.y, k = blockIdx.z;
     const size_t row = ((size_t)k * ny + j) * nx;
-    for (int e = tid; e < NC * CB; e += nthr) {
-      const int cc = e % CB, comp = e / CB, i = i0 + cc;
-      coef[comp][cc] = (i < nx) ? (R)__ldg(Qin + (size_t)comp * nc + row + i) : R(0);
+    // (cells beyond the row end: a copy of the row's first cell; padding zero)
+    for (int e = tid; e < NCP * CB; e += nthr) {
+      const int cc = e / NCP, c = e % NCP, i = i0 + cc;
+      coef[cc][c] = (c % NMP < NM) ? (R)__ldg(Qin + (size_t)((c / NMP) * NM + c % NMP) * nc + row + (i < nx ? i : 0))
+                                   : R(0);
     }
     __syncthreads();
     tile(i0, j, k, coef, nullptr);

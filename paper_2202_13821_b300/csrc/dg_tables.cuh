@@ -126,6 +126,21 @@ __host__ __device__ constexpr int tmode_index(int p, int q) {
                               : 9;  // (1, 2)
 }
 
+// index of the mode of degree <= 2 with exponents (a, b, c) (the inverse of
+// mode_exp on the first 10 modes)
+__host__ __device__ constexpr int mode_index2(int a, int b, int c) {
+  return (a + b + c == 0)         ? 0
+         : (a == 1 && b + c == 0) ? 1
+         : (b == 1 && a + c == 0) ? 2
+         : (c == 1 && a + b == 0) ? 3
+         : (a == 2)               ? 4
+         : (b == 2)               ? 5
+         : (c == 2)               ? 6
+         : (a == 1 && b == 1)     ? 7
+         : (a == 1 && c == 1)     ? 8
+                                  : 9;  // (0, 1, 1)
+}
+
 // tangential axes of a face normal to D, in increasing order
 __host__ __device__ constexpr int tan1(int D) { return D == 0 ? 1 : 0; }
 __host__ __device__ constexpr int tan2(int D) { return D == 2 ? 1 : 2; }
