@@ -1060,6 +1060,28 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       a.row = (size_t)r * nx;
       return a;
     };
+    // the tile gridDim.x further on, without per-tile divisions: tx advances
+    // by the remainder gr of gridDim.x / ntx, the row index k ny + j by the
+    // quotient gq (+1 on a carry); j wraps into k only when it passes ny
+    const unsigned gq = gridDim.x / ntx, gr = gridDim.x - gq * ntx;
+    auto next_at = [&](const TileAt& a) {
+      TileAt n;
+      unsigned tx = (unsigned)a.i0 / CB + gr, dr = gq;
+      if (tx >= ntx) {
+        tx -= ntx;
+        ++dr;
+      }
+      unsigned jj = (unsigned)a.j + dr, kk = (unsigned)a.k;
+      if (jj >= (unsigned)ny) {
+        kk += jj / (unsigned)ny;
+        jj %= (unsigned)ny;
+      }
+      n.i0 = (int)tx * CB;
+      n.j = (int)jj;
+      n.k = (int)kk;
+      n.row = ((size_t)kk * ny + jj) * nx;
+      return n;
+    };
     // (cells beyond the row end get a copy of the row's first cell: every
     // lane's flux input stays physical)
     auto issue = [&](const TileAt& a, int b) {
@@ -1129,7 +1151,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       const unsigned tn = t + gridDim.x;
       TileAt nxt = cur;
       if (tn < ntiles) {
-        nxt = at(tn);
+        nxt = next_at(cur);
         issue(nxt, b ^ 1);
         if (MODE != MODE_STAGE2) prefetch_faces(nxt);
       }
