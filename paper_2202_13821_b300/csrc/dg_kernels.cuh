@@ -269,11 +269,18 @@ __global__ void __launch_bounds__(FaceSmem<R, ORDER, NQ>::THREADS) __maxnreg__((
         }
       }
     }
+    // (16-byte stores: the variable's VP values are 16-byte aligned)
+    R vals[VP];
+#pragma unroll
+    for (int t = 0; t < VP; ++t) vals[t] = t < NT ? Vt[t] : (t < NT + NN ? Nt[t - NT] : R(0));
     R* dst = (side == 0 ? cL : cR)[ff] + v * VP;
 #pragma unroll
-    for (int t = 0; t < NT; ++t) dst[t] = Vt[t];
-#pragma unroll
-    for (int t = 0; t < NN; ++t) dst[NT + t] = Nt[t];
+    for (int q = 0; q < VP * (int)sizeof(R) / 16; ++q) {
+      if constexpr (sizeof(R) == 4)
+        reinterpret_cast<float4*>(dst)[q] = make_float4(vals[4 * q], vals[4 * q + 1], vals[4 * q + 2], vals[4 * q + 3]);
+      else
+        reinterpret_cast<double2*>(dst)[q] = make_double2(vals[2 * q], vals[2 * q + 1]);
+    }
   }
   __syncthreads();
 
@@ -390,16 +397,24 @@ __global__ void __launch_bounds__(FaceSmem<R, ORDER, NQ>::THREADS) __maxnreg__((
     }
   }
   __syncthreads();
+  // (in the widest vector units, up to 16 bytes, that the block or its F_t
+  // half and the face offsets are multiples of)
   const int nf = nx - i0 < FB ? nx - i0 : FB;
   R* const dst = G + ((size_t)D * nc + ((size_t)k * ny + j) * nx + i0) * (10 * NT);
   const R* const src = &Gs[0][0][0];
+  constexpr int BYTES = (FTO ? 5 : 10) * NT * (int)sizeof(R);  // bytes written per face
+  constexpr int UB = BYTES % 16 == 0 ? 16 : (BYTES % 8 == 0 ? 8 : 4);
+  using V = typename std::conditional<UB == 16, uint4, typename std::conditional<UB == 8, uint2, unsigned>::type>::type;
+  constexpr int PV = BYTES / UB, FS = 10 * NT * (int)sizeof(R) / UB;  // vectors per face, face stride
+  V* const dv = reinterpret_cast<V*>(dst);
+  const V* const sv = reinterpret_cast<const V*>(src);
   if (FTO) {
-    for (int e = tid; e < nf * 5 * NT; e += NTHR) {
-      const int ff = e / (5 * NT), r = e % (5 * NT);
-      dst[ff * (10 * NT) + 5 * NT + r] = src[ff * (10 * NT) + 5 * NT + r];
+    for (int e = tid; e < nf * PV; e += NTHR) {
+      const int ff = e / PV, r = e % PV;
+      dv[ff * FS + PV + r] = sv[ff * FS + PV + r];
     }
   } else {
-    for (int e = tid; e < nf * 10 * NT; e += NTHR) dst[e] = src[e];
+    for (int e = tid; e < nf * PV; e += NTHR) dv[e] = sv[e];
   }
 }
 
