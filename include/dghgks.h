@@ -192,8 +192,8 @@ int dghgks_status(dghgks_ctx* ctx, void* stream);
  * backward sweep per Gauss point), the projection and trace operators are
  * transposed exactly.  Uniform and rectilinear meshes.  They allocate
  * adjoint scratch on first use (face cotangents 3 x 2 x 5 N_m doubles per
- * cell, a state-sized buffer, per-CTA partials).  FP32-mixed contexts and
- * order 3 with n_q = 4 return DGHGKS_EUNSUP. */
+ * cell, a state-sized buffer, per-CTA partials).  Every order and Gauss
+ * count of dghgks_init; FP32 contexts return DGHGKS_EUNSUP. */
 
 /* (lamQ, dmu) = (dL/dQ, dL/dmu)^T lamL + (dL_t/dQ, dL_t/dmu)^T lamLt at Q for
  * the residual of dghgks_residual with the same dt.  lamQ (device, state

@@ -227,13 +227,16 @@ __global__ void __launch_bounds__(adj_fb<ORDER>() * NQ * NQ)
 // ---------------------------------------------------------------------------
 // Cell VJP: out = addA + addB + (volume part + the six faces' H) of the cell.
 // ---------------------------------------------------------------------------
+// (the forward kernel's layout: one lane per Gauss point, a cell over GW
+// warps; each warp reduces its points' share, the GW partial sums meet in
+// shared memory)
 template <int ORDER, int NQ>
 struct CellAdjSmem {
   using LY = CellLayout<ORDER, NQ>;
   static constexpr int NM = LY::NM, NC = 5 * NM, CB = LY::CB;
   static constexpr int NOP2 = (NC + LY::PG - 1) / LY::PG * LY::PG;
   static constexpr size_t coef = sizeof(double) * NC * CB;
-  static constexpr size_t red = sizeof(double) * CB * NOP2;
+  static constexpr size_t red = sizeof(double) * CB * LY::GW * NOP2;
   static constexpr size_t bytes = 3 * coef + red + sizeof(double) * LY::WARPS * 32;
 };
 
@@ -243,18 +246,19 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
                const size_t mu_offset) {
   using LY = CellLayout<ORDER, NQ>;
   using S = CellAdjSmem<ORDER, NQ>;
-  static_assert(LY::GW == 1, "the adjoint cell kernel handles up to 3^3 points per cell");
-  constexpr int NM = LY::NM, NP = LY::NP, NC = S::NC, CB = LY::CB, PG = LY::PG, NOP2 = S::NOP2;
+  constexpr int NM = LY::NM, NP = LY::NP, NC = S::NC, CB = LY::CB, PG = LY::PG, GW = LY::GW, NOP2 = S::NOP2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double(*cq)[CB] = reinterpret_cast<double(*)[CB]>(smem_raw);
   double(*cmuR)[CB] = reinterpret_cast<double(*)[CB]>(smem_raw + S::coef);
   double(*cmuT)[CB] = reinterpret_cast<double(*)[CB]>(smem_raw + 2 * S::coef);
-  double(*red)[NOP2] = reinterpret_cast<double(*)[NOP2]>(smem_raw + 3 * S::coef);
+  double(*red)[GW][NOP2] = reinterpret_cast<double(*)[GW][NOP2]>(smem_raw + 3 * S::coef);
   double* mured = reinterpret_cast<double*>(smem_raw + 3 * S::coef + S::red);
 
   const int tid = threadIdx.x, nthr = LY::WARPS * 32;
-  const int lane = tid & 31, lg = lane % PG;
-  const int cb = (tid >> 5) * LY::CPW + lane / PG;
+  const int lane = tid & 31, lg = lane % PG, warp = tid >> 5;
+  const int cb = GW == 1 ? warp * LY::CPW + lane / PG : warp / GW;  // cell of this lane within the CTA
+  const int gw = GW == 1 ? 0 : warp % GW;                            // which warp of the cell
+  const int pidx = gw * 32 + lg;                                      // Gauss point of this lane
   const int i0 = blockIdx.x * CB, j = blockIdx.y, k = blockIdx.z;
   const int nx = m.nx, ny = m.ny, nz = m.nz;
   const long long nc = m.ncell;
@@ -277,8 +281,8 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
   }
   __syncthreads();
 
-  const bool active = (lg < NP) && (i0 + cb < nx);
-  const int pp = active ? lg : 0;
+  const bool active = (pidx < NP) && (i0 + cb < nx);
+  const int pp = active ? pidx : 0;
   const int pa[3] = {pp / (NQ * NQ), (pp / NQ) % NQ, pp % NQ};
   double L1[3][ORDER + 1], dL1[3][ORDER + 1];
 #pragma unroll
@@ -357,7 +361,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
     }
     double outv[1];
     group_reduce<PG, PG>(val, outv, lg);
-    red[cb][c0 + lg] = outv[0];
+    red[cb][gw][c0 + lg] = outv[0];
   }
   __syncthreads();
 
@@ -366,7 +370,9 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
     const int cc = o % CB, comp = o / CB, i = i0 + cc;
     if (i >= nx) continue;
     const size_t cell = row + i, idx = (size_t)comp * nc + cell;
-    double s = red[cc][comp];
+    double s = red[cc][0][comp];
+#pragma unroll
+    for (int g = 1; g < GW; ++g) s += red[cc][g][comp];
 #pragma unroll
     for (int D = 0; D < 3; ++D) {
       size_t up;

@@ -43,6 +43,7 @@ cudaError_t adjoint_set_attrs(int order, int nq) {
   if (order == 2 && nq == 2) return attrs<2, 2>();
   if (order == 2 && nq == 3) return attrs<2, 3>();
   if (order == 3 && nq == 3) return attrs<3, 3>();
+  if (order == 3 && nq == 4) return attrs<3, 4>();
   return cudaErrorInvalidValue;
 }
 
@@ -52,6 +53,7 @@ void adjoint_vjp(int order, int nq, const double* Q, const GasPar<double>& g, co
   else if (order == 2 && nq == 2) vjp<2, 2>(Q, g, m, io, s);
   else if (order == 2 && nq == 3) vjp<2, 3>(Q, g, m, io, s);
   else if (order == 3 && nq == 3) vjp<3, 3>(Q, g, m, io, s);
+  else if (order == 3 && nq == 4) vjp<3, 4>(Q, g, m, io, s);
 }
 
 long long adjoint_face_ctas(int order, int nx, int ny, int nz) {
@@ -69,6 +71,7 @@ void adjoint_ek_vjp(int order, int nq, const double* Q, const MeshDev& m, double
   else if (order == 2 && nq == 2) k_ek_vjp<2, 2><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, m, scale, out);
   else if (order == 2 && nq == 3) k_ek_vjp<2, 3><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, m, scale, out);
   else if (order == 3 && nq == 3) k_ek_vjp<3, 3><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, m, scale, out);
+  else if (order == 3 && nq == 4) k_ek_vjp<3, 4><<<kRedBlocksAdj, RED_THREADS, 0, s>>>(Q, m, scale, out);
 }
 
 }  // namespace dghgks

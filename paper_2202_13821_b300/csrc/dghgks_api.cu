@@ -802,13 +802,12 @@ int dghgks_profile_read(dghgks_ctx* c, double* ms, int64_t* launches) {
 
 static int adj_prepare(dghgks_ctx* c) {
   if (c->precision != DGHGKS_FP64) return fail(c, DGHGKS_EUNSUP, "the adjoint needs an FP64 context");
-  if (c->order > 3 || (c->order == 3 && c->nq != 3))
-    return fail(c, DGHGKS_EUNSUP, "the adjoint supports orders 1 and 2, and order 3 with n_q = 3");
+  if (c->order > 3) return fail(c, DGHGKS_EUNSUP, "the adjoint supports orders 1 to 3");
   if (c->adjH) return DGHGKS_OK;
   const size_t nc = (size_t)c->ncell;
   const size_t state = sizeof(double) * 5 * (size_t)c->nm * nc;
   const size_t fblocks = (size_t)adjoint_face_ctas(c->order, c->n[0], c->n[1], c->n[2]);
-  const size_t cblocks = (size_t)((c->n[0] + 7) / 8) * c->n[1] * c->n[2];  // cell CTAs own >= 8 cells
+  const size_t cblocks = (size_t)((c->n[0] + 3) / 4) * c->n[1] * c->n[2];  // cell CTAs own >= 4 cells
   c->adjMuN = 3 * fblocks + cblocks;
   int rc = cuda_check(c, adjoint_set_attrs(c->order, c->nq), "adjoint attributes");
   if (!rc) rc = cuda_check(c, cudaMalloc(&c->adjH, 6 * state), "cudaMalloc(face cotangents)");
@@ -886,8 +885,7 @@ int dghgks_adjoint_step(dghgks_ctx* c, const double* Qn, const double* lam_next,
 
 int dghgks_kinetic_energy_vjp(dghgks_ctx* c, const double* Q, double rho0, double* dEk_dQ, void* stream) {
   if (!c) return DGHGKS_EARG;
-  if (c->order > 3 || (c->order == 3 && c->nq != 3))
-    return fail(c, DGHGKS_EUNSUP, "the adjoint supports orders 1 and 2, and order 3 with n_q = 3");
+  if (c->order > 3) return fail(c, DGHGKS_EUNSUP, "the adjoint supports orders 1 to 3");
   if (!Q || !dEk_dQ || dEk_dQ == Q) return fail(c, DGHGKS_EARG, "bad argument");
   if (!(rho0 > 0)) return fail(c, DGHGKS_EARG, "rho0 must be > 0");
   adjoint_ek_vjp(c->order, c->nq, Q, mesh_dev(c), vol_scale(c) / (rho0 * c->omega), dEk_dQ,

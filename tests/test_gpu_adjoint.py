@@ -51,6 +51,10 @@ CASES = [
     dict(order=2, nq=3, n=(4, 3, 5), mu=1e-2, Pr=0.72, tau_eps=0.0, state="random"),
     dict(order=2, nq=2, n=(6, 5, 4), mu=1 / 1600, Pr=0.72, tau_eps=0.0, state="tgv"),
     dict(order=1, nq=2, n=(6, 6, 6), mu=0.0, Pr=1.0, tau_eps=0.01, state="adv"),
+    # P3 with n_q = 4: a cell's 64 points over two warps, cell CTAs of 4 cells
+    # (ragged at nx = 5 and 3)
+    dict(order=3, nq=4, n=(5, 3, 3), mu=1e-2, Pr=0.72, tau_eps=0.0, state="tgv"),
+    dict(order=3, nq=4, n=(3, 4, 3), mu=5e-3, Pr=0.72, tau_eps=0.0, state="random", nodes=True),
 ]
 
 
@@ -99,8 +103,8 @@ def test_residual_vjp_dot_product(torch, api, orc, case):
     assert abs(lhs - rhs) <= 1e-10 * scale, (lhs, rhs, scale)
 
 
-@pytest.mark.parametrize("case", CASES[1:7], ids=lambda c: f"P{c['order']}-{c['state']}"
-                                                        + ("-rect" if c.get("nodes") else ""))
+@pytest.mark.parametrize("case", CASES[1:7] + CASES[8:10], ids=lambda c: f"P{c['order']}nq{c['nq']}-{c['state']}"
+                                                                        + ("-rect" if c.get("nodes") else ""))
 def test_adjoint_step_dot_product(torch, api, orc, case):
     s, pb, Q = make_case(api, orc, case)
     dt = 2e-3
