@@ -167,6 +167,28 @@ def test_fp32_mixed_residual_every_layout(torch, api, orc, order, nq, precision)
     print(f"P{order} n_q={nq} precision {precision}: max err / scale L {worst[0]:.2e}, L_t {worst[1]:.2e}")
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rows_longer_than_the_grid(torch, api, orc, precision):
+    """Persistent cell CTAs take the tiles of 8 cells gridDim.x apart and step a tile's coordinates
+    from the previous one.  2400 x 1 x 2 cells: 300 tiles per row, more than the resident CTAs of a
+    B300 (148 in FP64, 296 in FP32), so a CTA's next tile lies in the same row or, past the row's end,
+    in the next row, which here is the next z plane (the row index wraps into the plane index).  FP64:
+    the parity bound of the other residual tests; FP32-mixed: 2e-5 of the oracle's magnitude scale."""
+    from paper_2202_13821_b300 import inputs
+
+    n = (2400, 1, 2)
+    s, pb = make(api, orc, n, order=2, nq=3, mu=1 / 1600, Pr=0.72, precision=precision, **TGV)
+    Q = inputs.modal_state(inputs.tgv_prim, n, 2, TGV["lo"], TGV["hi"], perturb=1e-3)
+    L, Lt, ref = residual_pair(torch, s, pb, orc, Q, 1.3e-3)
+    if precision == 0:
+        assert_residual_parity(L, Lt, ref)
+    else:
+        for a, b, sc in ((L, ref[0], ref[2]), (Lt, ref[1], ref[3])):
+            err = np.abs(a - b).reshape(5, -1).max(axis=1)
+            scale = np.abs(sc).reshape(5, -1).max(axis=1)
+            assert np.all(err <= 2e-5 * scale), err / scale
+
+
 @pytest.mark.parametrize("order,nq,case", [(1, 2, "adv"), (2, 3, "tgv"), (3, 4, "tgv")])
 def test_s2o4_step_parity(torch, api, orc, order, nq, case):
     from paper_2202_13821_b300 import inputs
