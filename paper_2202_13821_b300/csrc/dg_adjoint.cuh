@@ -48,8 +48,10 @@ DG_HD double inv_mass(int mm, double vol) {
 // ---------------------------------------------------------------------------
 // Face VJP: H[D][side][comp][face] = sum over the face's Gauss points of the
 // trace transpose of the traces' cotangents; mu_part[block] = viscosity part.
+// FTO: the cotangent of L is zero (io.cLA = io.cLB = 0: stage 2 of the S2O4
+// adjoint), so the point sweeps differentiate F_t alone.
 // ---------------------------------------------------------------------------
-template <int ORDER, int NQ, int D>
+template <int ORDER, int NQ, int D, bool FTO = false>
 __global__ void __launch_bounds__(adj_fb<ORDER>() * NQ * NQ)
     k_face_vjp(const double* __restrict__ Q, const GasPar<double> gp, const MeshDev m, const AdjIO io,
                const size_t mu_offset) {
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(adj_fb<ORDER>() * NQ * NQ)
       mT = iM * (io.cTA * a + io.cTB * b);
     }
     cq[side][c][ff] = q;
-    cmu[side * 2][c][ff] = mR;
+    if (!FTO) cmu[side * 2][c][ff] = mR;
     cmu[side * 2 + 1][c][ff] = mT;
   }
   __syncthreads();
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(adj_fb<ORDER>() * NQ * NQ)
         gD += c * (dpn * La[n1] * Lb[n2]);
         g1 += c * (pn * dLa[n1] * Lb[n2]);
         g2 += c * (pn * La[n1] * dLb[n2]);
-        lF[v] += sg * B * cmu[side * 2][v * NM + mm][f];
+        if (!FTO) lF[v] += sg * B * cmu[side * 2][v * NM + mm][f];
         lT[v] += sg * B * cmu[side * 2 + 1][v * NM + mm][f];
       }
       q[side][v] = s0;
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(adj_fb<ORDER>() * NQ * NQ)
   const double Flb[5] = {lF[0], lF[1 + A0], lF[1 + A1], lF[1 + A2], lF[4]};
   const double Ftlb[5] = {lT[0], lT[1 + A0], lT[1 + A1], lT[1 + A2], lT[4]};
   double qlb[2][5], dqlb[2][3][5], gmu = 0.0;
-  iface_flux_vjp(ql0[0], dql0[0], ql0[1], dql0[1], gp, Flb, Ftlb, qlb[0], dqlb[0], qlb[1], dqlb[1], gmu);
+  iface_flux_vjp<double, FTO>(ql0[0], dql0[0], ql0[1], dql0[1], gp, Flb, Ftlb, qlb[0], dqlb[0], qlb[1], dqlb[1], gmu);
   if (!active) gmu = 0.0;
   // back to global variables and axes: local index of a global momentum component
   const int loc[3] = {(0 - A0 + 3) % 3, (1 - A0 + 3) % 3, (2 - A0 + 3) % 3};
@@ -240,7 +242,8 @@ struct CellAdjSmem {
   static constexpr size_t bytes = 3 * coef + red + sizeof(double) * LY::WARPS * 32;
 };
 
-template <int ORDER, int NQ>
+// (FTO as for the face VJP)
+template <int ORDER, int NQ, bool FTO = false>
 __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
     k_cell_vjp(const double* __restrict__ Q, const GasPar<double> gp, const MeshDev m, const AdjIO io,
                const size_t mu_offset) {
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
       mT = iM * (io.cTA * a + io.cTB * b);
     }
     cq[comp][cc] = q;
-    cmuR[comp][cc] = mR;
+    if (!FTO) cmuR[comp][cc] = mR;
     cmuT[comp][cc] = mT;
   }
   __syncthreads();
@@ -314,7 +317,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         g[d] += c * dB[d];
-        f3[d] += dB[d] * cmuR[v * NM + mm][cb];
+        if (!FTO) f3[d] += dB[d] * cmuR[v * NM + mm][cb];
         t3[d] += dB[d] * cmuT[v * NM + mm][cb];
       }
     }
@@ -329,7 +332,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32)
 
   // reverse mode of the interior flux (gks_point_adj.cuh): one backward sweep
   double gq[5], gdq[3][5], gmu = 0.0;
-  interior_flux_vjp(q, dq, gp, lF, lT, gq, gdq, gmu);
+  interior_flux_vjp<double, FTO>(q, dq, gp, lF, lT, gq, gdq, gmu);
   if (!active) {
     gmu = 0.0;
 #pragma unroll

@@ -11,30 +11,43 @@ namespace dghgks {
 namespace {
 constexpr int kRedBlocksAdj = 148 * 8;
 
-template <int ORDER, int NQ>
-cudaError_t attrs() {
+template <int ORDER, int NQ, bool FTO>
+cudaError_t attrs_k() {
   cudaError_t e = cudaSuccess;
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   const int fb = (int)FaceAdjSmem<ORDER, NQ>::bytes, cb = (int)CellAdjSmem<ORDER, NQ>::bytes;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 0>, a, fb);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 1>, a, fb);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 2>, a, fb);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cell_vjp<ORDER, NQ>, a, cb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 0, FTO>, a, fb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 1, FTO>, a, fb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_vjp<ORDER, NQ, 2, FTO>, a, fb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cell_vjp<ORDER, NQ, FTO>, a, cb);
   return e;
 }
-
 template <int ORDER, int NQ>
-void vjp(const double* Q, const GasPar<double>& g, const MeshDev& m, const AdjIO& io, cudaStream_t s) {
+cudaError_t attrs() {
+  const cudaError_t e = attrs_k<ORDER, NQ, false>();
+  return e == cudaSuccess ? attrs_k<ORDER, NQ, true>() : e;
+}
+
+template <int ORDER, int NQ, bool FTO>
+void vjp_k(const double* Q, const GasPar<double>& g, const MeshDev& m, const AdjIO& io, cudaStream_t s) {
   constexpr int FBA = adj_fb<ORDER>();
   const dim3 fgrid((m.nx + FBA - 1) / FBA, m.ny, m.nz), fblock(FBA * NQ * NQ);
   const size_t fblocks = (size_t)fgrid.x * fgrid.y * fgrid.z;
   const size_t fbytes = FaceAdjSmem<ORDER, NQ>::bytes;
-  k_face_vjp<ORDER, NQ, 0><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 0 * fblocks);
-  k_face_vjp<ORDER, NQ, 1><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 1 * fblocks);
-  k_face_vjp<ORDER, NQ, 2><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 2 * fblocks);
+  k_face_vjp<ORDER, NQ, 0, FTO><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 0 * fblocks);
+  k_face_vjp<ORDER, NQ, 1, FTO><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 1 * fblocks);
+  k_face_vjp<ORDER, NQ, 2, FTO><<<fgrid, fblock, fbytes, s>>>(Q, g, m, io, 2 * fblocks);
   using LY = CellLayout<ORDER, NQ>;
   const dim3 cgrid((m.nx + LY::CB - 1) / LY::CB, m.ny, m.nz), cblock(LY::WARPS * 32);
-  k_cell_vjp<ORDER, NQ><<<cgrid, cblock, CellAdjSmem<ORDER, NQ>::bytes, s>>>(Q, g, m, io, 3 * fblocks);
+  k_cell_vjp<ORDER, NQ, FTO><<<cgrid, cblock, CellAdjSmem<ORDER, NQ>::bytes, s>>>(Q, g, m, io, 3 * fblocks);
+}
+// a zero cotangent of L (stage 2 of the S2O4 adjoint) takes the F_t-only sweeps
+template <int ORDER, int NQ>
+void vjp(const double* Q, const GasPar<double>& g, const MeshDev& m, const AdjIO& io, cudaStream_t s) {
+  if (io.cLA == 0.0 && io.cLB == 0.0)
+    vjp_k<ORDER, NQ, true>(Q, g, m, io, s);
+  else
+    vjp_k<ORDER, NQ, false>(Q, g, m, io, s);
 }
 }  // namespace
 

@@ -551,10 +551,13 @@ DG_HD void iface_side_b(int SGN, const R q[5], const R dq[3][5], const GasPar<R>
 }
 
 // ---- interface equilibrium and fitted flux: cotangents of F, F_t -> of the sums and mu ----
-template <class R>
+// FTO: the cotangent of F is zero (stage 2 of the S2O4 adjoint, where only
+// L_t enters): Fb is not read, and F, the heat-flux term (F only) and every
+// product with the zero cotangent are left out of both sweeps.
+template <class R, bool FTO = false>
 DG_HD void iface_finish_b(const SideSums<R>& S, const GasPar<R>& g, const R Fb[5], const R Ftb[5], SideSums<R>& Sb,
                           R& mub) {
-  const bool pr_fix = (g.pr_fix != R(0));
+  const bool pr_fix = !FTO && (g.pr_fix != R(0));
   // forward recomputation (iface_finish)
   Prim<R> p0;
   prim_of(S.Q0, g.gm1, p0);
@@ -593,7 +596,8 @@ DG_HD void iface_finish_b(const SideSums<R>& S, const GasPar<R>& g, const R Fb[5
   R Fc[5], Ftc[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    Fc[k] = r0 * (wF[0] * V1[k] + wF[1] * V2[k] + wF[2] * V3[k]) + wF[3] * V4[k] + wF[4] * V5[k] + wF[5] * V6[k];
+    if (!FTO)
+      Fc[k] = r0 * (wF[0] * V1[k] + wF[1] * V2[k] + wF[2] * V3[k]) + wF[3] * V4[k] + wF[4] * V5[k] + wF[5] * V6[k];
     Ftc[k] = r0 * (wFt[0] * V1[k] + wFt[1] * V2[k] + wFt[2] * V3[k]) + wFt[3] * V4[k] + wFt[4] * V5[k] +
              wFt[5] * V6[k];
   }
@@ -621,7 +625,7 @@ DG_HD void iface_finish_b(const SideSums<R>& S, const GasPar<R>& g, const R Fb[5
   for (int j = 0; j < 6; ++j) wFb[j] = wFtb[j] = R(0);
   // F = S_U Fc, Ft = S_U Ftc
   R Fcb[5] = {R(0), R(0), R(0), R(0), R(0)}, Ftcb[5] = {R(0), R(0), R(0), R(0), R(0)};
-  add_uncentred_b<true>(Fc, U, V, W, hs2, Fb, Fcb, p0b.U, p0b.V, p0b.W, hs2b);
+  if (!FTO) add_uncentred_b<true>(Fc, U, V, W, hs2, Fb, Fcb, p0b.U, p0b.V, p0b.W, hs2b);
   add_uncentred_b<true>(Ftc, U, V, W, hs2, Ftb, Ftcb, p0b.U, p0b.V, p0b.W, hs2b);
   R V1b[5], V2b[5], V3b[5], V4b[5], V5b[5], V6b[5], Wabb[5];
 #pragma unroll
@@ -649,6 +653,22 @@ DG_HD void iface_finish_b(const SideSums<R>& S, const GasPar<R>& g, const R Fb[5
   // Fc = r0 (wF0 V1 + wF1 V2 + wF2 V3) + wF3 V4 + wF4 V5 + wF5 V6, Ftc alike
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
+    if constexpr (FTO) {
+      r0b += Ftcb[k] * (wFt[0] * V1[k] + wFt[1] * V2[k] + wFt[2] * V3[k]);
+      wFtb[0] += Ftcb[k] * r0 * V1[k];
+      wFtb[1] += Ftcb[k] * r0 * V2[k];
+      wFtb[2] += Ftcb[k] * r0 * V3[k];
+      wFtb[3] += Ftcb[k] * V4[k];
+      wFtb[4] += Ftcb[k] * V5[k];
+      wFtb[5] += Ftcb[k] * V6[k];
+      V1b[k] += r0 * (wFt[0] * Ftcb[k]);
+      V2b[k] += r0 * (wFt[1] * Ftcb[k]);
+      V3b[k] += r0 * (wFt[2] * Ftcb[k]);
+      V4b[k] += wFt[3] * Ftcb[k];
+      V5b[k] += wFt[4] * Ftcb[k];
+      V6b[k] += wFt[5] * Ftcb[k];
+      continue;
+    }
     r0b += Fcb[k] * (wF[0] * V1[k] + wF[1] * V2[k] + wF[2] * V3[k]) +
            Ftcb[k] * (wFt[0] * V1[k] + wFt[1] * V2[k] + wFt[2] * V3[k]);
     wFb[0] += Fcb[k] * r0 * V1[k];
@@ -727,26 +747,53 @@ DG_HD void iface_finish_b(const SideSums<R>& S, const GasPar<R>& g, const R Fb[5
 }
 
 // VJP of iface_flux: cotangents of (F, F_t) -> of (qL, dqL, qR, dqR) (overwritten) and mu (+=).
-template <class R>
+// (FTO: zero cotangent of F, Fb not read; the side sums of the heat-flux term,
+// which enters F only, are then neither formed nor differentiated)
+template <class R, bool FTO = false>
 DG_HD void iface_flux_vjp(const R qL[5], const R dqL[3][5], const R qR[5], const R dqR[3][5], const GasPar<R>& g,
                           const R Fb[5], const R Ftb[5], R qLb[5], R dqLb[3][5], R qRb[5], R dqRb[3][5], R& mub) {
-  const bool pr_fix = (g.pr_fix != R(0));
+  const bool pr_fix = !FTO && (g.pr_fix != R(0));
   SideSums<R> S, Sb;
   iface_zero(S);
   iface_side<R>(1, qL, dqL, g, pr_fix, S);
   iface_side<R>(-1, qR, dqR, g, pr_fix, S);
-  iface_finish_b(S, g, Fb, Ftb, Sb, mub);
+  iface_finish_b<R, FTO>(S, g, Fb, Ftb, Sb, mub);
   iface_side_b<R>(1, qL, dqL, g, pr_fix, Sb, qLb, dqLb);
   iface_side_b<R>(-1, qR, dqR, g, pr_fix, Sb, qRb, dqRb);
 }
 
 // ---- interior flux of one direction ----
-template <int D, class R>
+// (FTO: zero cotangent of F, Fb not read: only F_t = rho <u_d (A . psi) psi>
+// is recomputed and differentiated)
+template <int D, bool FTO, class R>
 DG_HD void interior_dir_b(const CTab<R>& t, const Prim<R>& p, R hs2, const R a[3][5], const R aU[5], const R A[5],
                           const R Wau[5], R tau, const GasPar<R>& g, const R Fb[5], const R Ftb[5], CTabB<R>& tb,
                           Prim<R>& pb, R& hs2b, R ab[3][5], R aUb[5], R Ab[5], R Waub[5], R& taub) {
-  // forward recomputation (interior_dir)
   const R Ud = (D == 0) ? p.U : (D == 1) ? p.V : p.W;
+  if constexpr (FTO) {
+    // F_t = S_U (rho m2), m2 = -Ud Wau + <c_d (A . psi'') psi''>
+    R m2[5], Ftc[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) m2[k] = -Ud * Wau[k];
+    cmom_a_e<true, D>(t, A, m2);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Ftc[k] = p.rho * m2[k];
+    R Udb = R(0), Ftcb[5] = {R(0), R(0), R(0), R(0), R(0)}, m2b[5];
+    add_uncentred_b<true>(Ftc, p.U, p.V, p.W, hs2, Ftb, Ftcb, pb.U, pb.V, pb.W, hs2b);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      pb.rho += Ftcb[k] * m2[k];
+      m2b[k] = Ftcb[k] * p.rho;
+      Udb += -m2b[k] * Wau[k];
+      Waub[k] += -Ud * m2b[k];
+    }
+    cmom_a_e_b<true, D>(t, A, m2b, tb, Ab);
+    if (D == 0) pb.U += Udb;
+    if (D == 1) pb.V += Udb;
+    if (D == 2) pb.W += Udb;
+    return;
+  }
+  // forward recomputation (interior_dir)
   R m0[5] = {R(0), R(0), R(0), R(0), R(0)}, m1[5], m2[5];
   cmom_psi<true, 0, 0, 0>(t, Ud, m0);
   cmom_psi<true, D == 0, D == 1, D == 2>(t, R(1), m0);
@@ -817,7 +864,7 @@ DG_HD void interior_dir_b(const CTab<R>& t, const Prim<R>& p, R hs2, const R a[3
 }
 
 // VJP of interior_flux: cotangents of (F[3][5], F_t[3][5]) -> of (q, dq) (overwritten) and mu (+=).
-template <class R>
+template <class R, bool FTO = false>
 DG_HD void interior_flux_vjp(const R q[5], const R dq[3][5], const GasPar<R>& g, const R Fb[3][5],
                              const R Ftb[3][5], R qb[5], R dqb[3][5], R& mub) {
   // forward recomputation (interior_flux)
@@ -850,9 +897,9 @@ DG_HD void interior_flux_vjp(const R q[5], const R dq[3][5], const GasPar<R>& g,
 #pragma unroll
     for (int i = 0; i < 3; ++i) ab[i][k] = R(0);
   }
-  interior_dir_b<2>(t, p, hs2, a, aU, A, Wau, tau, g, Fb[2], Ftb[2], tb, pb, hs2b, ab, aUb, Ab, Waub, taub);
-  interior_dir_b<1>(t, p, hs2, a, aU, A, Wau, tau, g, Fb[1], Ftb[1], tb, pb, hs2b, ab, aUb, Ab, Waub, taub);
-  interior_dir_b<0>(t, p, hs2, a, aU, A, Wau, tau, g, Fb[0], Ftb[0], tb, pb, hs2b, ab, aUb, Ab, Waub, taub);
+  interior_dir_b<2, FTO>(t, p, hs2, a, aU, A, Wau, tau, g, Fb[2], Ftb[2], tb, pb, hs2b, ab, aUb, Ab, Waub, taub);
+  interior_dir_b<1, FTO>(t, p, hs2, a, aU, A, Wau, tau, g, Fb[1], Ftb[1], tb, pb, hs2b, ab, aUb, Ab, Waub, taub);
+  interior_dir_b<0, FTO>(t, p, hs2, a, aU, A, Wau, tau, g, Fb[0], Ftb[0], tb, pb, hs2b, ab, aUb, Ab, Waub, taub);
   // tau = 2 mu lam / rho + tau_add
   mub += taub * fdiv(R(2) * p.lam, p.rho);
   pb.lam += taub * fdiv(R(2) * g.mu, p.rho);

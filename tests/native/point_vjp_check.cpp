@@ -2,8 +2,11 @@
 // (csrc/gks_point_adj.cuh) against forward-mode dual numbers run through the
 // forward flux templates (csrc/gks_point.cuh): for random physical states and
 // random output cotangents w, every component of the VJP J^T w must equal the
-// directional derivative w . (J e_j).  Prints the largest relative error per
-// case; exit status 1 if any exceeds 1e-11.
+// directional derivative w . (J e_j); the F_t-only sweeps (FTO: a zero
+// cotangent of F, the S2O4 adjoint's second stage) are given a random F
+// cotangent, which they must ignore, and compared with w . (J e_j) for the
+// F_t part of w alone.  Prints the largest relative error per case; exit
+// status 1 if any exceeds 1e-11.
 #define DG_HD inline
 #include <cmath>
 #include <cstdio>
@@ -69,6 +72,7 @@ static GasPar<R> gas(double mu, double pr, double dt, double tau_eps) {
   return g;
 }
 
+template <bool FTO>
 static double face_case(double mu, double pr, double dt, double tau_eps) {
   double qL[5], dqL[3][5], qR[5], dqR[3][5], Fb[5], Ftb[5];
   state(qL, dqL);
@@ -79,7 +83,7 @@ static double face_case(double mu, double pr, double dt, double tau_eps) {
   }
   const GasPar<double> g = gas<double>(mu, pr, dt, tau_eps);
   double qLb[5], dqLb[3][5], qRb[5], dqRb[3][5], mub = 0.0;
-  iface_flux_vjp(qL, dqL, qR, dqR, g, Fb, Ftb, qLb, dqLb, qRb, dqRb, mub);
+  iface_flux_vjp<double, FTO>(qL, dqL, qR, dqR, g, Fb, Ftb, qLb, dqLb, qRb, dqRb, mub);
   double rev[41];
   for (int k = 0; k < 5; ++k) {
     rev[k] = qLb[k];
@@ -105,13 +109,14 @@ static double face_case(double mu, double pr, double dt, double tau_eps) {
     gd.mu = Dl(mu, j == 40);
     iface_flux(xL, dxL, xR, dxR, gd, F, Ft);
     double fwd = 0.0;
-    for (int k = 0; k < 5; ++k) fwd += Fb[k] * F[k].d + Ftb[k] * Ft[k].d;
+    for (int k = 0; k < 5; ++k) fwd += (FTO ? 0.0 : Fb[k] * F[k].d) + Ftb[k] * Ft[k].d;
     err = std::fmax(err, std::fabs(fwd - rev[j]));
     scale = std::fmax(scale, std::fabs(fwd));
   }
   return err / scale;
 }
 
+template <bool FTO>
 static double cell_case(double mu, double pr, double dt, double tau_eps) {
   double q[5], dq[3][5], Fb[3][5], Ftb[3][5];
   state(q, dq);
@@ -122,7 +127,7 @@ static double cell_case(double mu, double pr, double dt, double tau_eps) {
     }
   const GasPar<double> g = gas<double>(mu, pr, dt, tau_eps);
   double qb[5], dqb[3][5], mub = 0.0;
-  interior_flux_vjp(q, dq, g, Fb, Ftb, qb, dqb, mub);
+  interior_flux_vjp<double, FTO>(q, dq, g, Fb, Ftb, qb, dqb, mub);
   double rev[21];
   for (int k = 0; k < 5; ++k) {
     rev[k] = qb[k];
@@ -141,7 +146,7 @@ static double cell_case(double mu, double pr, double dt, double tau_eps) {
     interior_flux(x, dx, gd, F, Ft);
     double fwd = 0.0;
     for (int d = 0; d < 3; ++d)
-      for (int k = 0; k < 5; ++k) fwd += Fb[d][k] * F[d][k].d + Ftb[d][k] * Ft[d][k].d;
+      for (int k = 0; k < 5; ++k) fwd += (FTO ? 0.0 : Fb[d][k] * F[d][k].d) + Ftb[d][k] * Ft[d][k].d;
     err = std::fmax(err, std::fabs(fwd - rev[j]));
     scale = std::fmax(scale, std::fabs(fwd));
   }
@@ -154,10 +159,13 @@ int main() {
   double worst = 0.0;
   for (auto& c : cases)
     for (int rep = 0; rep < 4; ++rep) {
-      const double ef = face_case(c[0], c[1], c[2], c[3]);
-      const double ec = cell_case(c[0], c[1], c[2], c[3]);
-      std::printf("mu %g Pr %g dt %g tau_eps %g: face %.3e cell %.3e\n", c[0], c[1], c[2], c[3], ef, ec);
-      worst = std::fmax(worst, std::fmax(ef, ec));
+      const double ef = face_case<false>(c[0], c[1], c[2], c[3]);
+      const double ec = cell_case<false>(c[0], c[1], c[2], c[3]);
+      const double ef2 = face_case<true>(c[0], c[1], c[2], c[3]);
+      const double ec2 = cell_case<true>(c[0], c[1], c[2], c[3]);
+      std::printf("mu %g Pr %g dt %g tau_eps %g: face %.3e cell %.3e; F_t only: face %.3e cell %.3e\n", c[0], c[1],
+                  c[2], c[3], ef, ec, ef2, ec2);
+      worst = std::fmax(std::fmax(worst, std::fmax(ef, ec)), std::fmax(ef2, ec2));
     }
   std::printf("worst %.3e\n", worst);
   return worst <= 1e-11 ? 0 : 1;

@@ -1,7 +1,8 @@
 """The hand-written reverse mode of the point fluxes (csrc/gks_point_adj.cuh, used by the adjoint
 kernels) against forward-mode dual numbers through the forward flux templates, compiled for the
 host: every component of J^T w, for random physical states and cotangents, Pr = 1 and 0.72,
-mu > 0 and mu = 0 with tau_eps > 0 (tests/native/point_vjp_check.cpp)."""
+mu > 0 and mu = 0 with tau_eps > 0, for the full sweeps and for the F_t-only sweeps of the adjoint's
+second stage (tests/native/point_vjp_check.cpp)."""
 import os
 import subprocess
 
