@@ -183,7 +183,9 @@ int dghgks_l2_diff(dghgks_ctx* ctx, const double* A, const double* B, int var, d
 
 /* Synchronise `stream` and report the device error flag: DGHGKS_EPHYS if a
  * non-physical state was met since the last check (the flag is then
- * cleared), DGHGKS_ECUDA on a CUDA error, else 0. */
+ * cleared), DGHGKS_ECUDA on a CUDA error or if a cell kernel gave up a
+ * shared-memory barrier wait (bounded at 2 s; its results are then invalid),
+ * else 0. */
 int dghgks_status(dghgks_ctx* ctx, void* stream);
 
 /* ---- adjoint (reverse mode, FP64 contexts only; the paper has none) ----

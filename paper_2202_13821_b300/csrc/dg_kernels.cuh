@@ -44,7 +44,9 @@
 // Each face is computed exactly once and written by exactly one CTA, and
 // every residual coefficient is summed in a fixed order: results are
 // bit-reproducible from run to run (no floating-point atomics).
-// A non-physical state (rho <= 0 or p <= 0) sets bit 0 of *flag.
+// A non-physical state (rho <= 0 or p <= 0) sets bit 0 of *flag; a wait of
+// the persistent cell kernel on one of its shared-memory barriers that has
+// not completed within 2 s (it never should) sets bit 1 and ends the kernel.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -493,17 +495,21 @@ struct CellSmem {
   // 5 variables' NM modes, each variable padded to NMP values (v NMP + n), so
   // that a lane reads a variable's modes with 16-byte loads
   static constexpr int NMP = (NM + 3) / 4 * 4, NCP = 5 * NMP;
-  // GW = 1: two staging buffers of the input type (cp.async targets), plus a
+  // GW = 1: NBUF staging buffers of the input type (cp.async targets), plus a
   // converted copy when the input is not in the flux precision; GW > 1: one
   // buffer in the flux precision.
-  static constexpr size_t raw = LY::GW == 1 ? 2 * sizeof(Tin) * NCP * CB : 0;
+  // (three when DECOUPLED: a warp may run one tile ahead of the slowest warp
+  // of its CTA; two at stage 2, which keeps a CTA barrier per tile)
+  static constexpr bool DECOUPLED = MODE != MODE_STAGE2;
+  static constexpr int NBUF = DECOUPLED ? 3 : 2;
+  static constexpr size_t raw = LY::GW == 1 ? NBUF * sizeof(Tin) * NCP * CB : 0;
   static constexpr size_t cvt = (LY::GW == 1 && std::is_same<Tin, R>::value) ? 0 : sizeof(R) * NCP * CB;
   // cross-warp partial sums (only when a cell spans two warps)
   static constexpr size_t red = LY::GW == 1 ? 0 : sizeof(R) * CB * LY::GW * 2 * LY::NOP;
   // GW = 1: the outputs of a tile (NKO kinds: two, one at stage 2; NC x CB),
-  // double-buffered, so that they leave as rows of CB consecutive cells
+  // in NBUF buffers, so that they leave as rows of CB consecutive cells
   static constexpr int NKO = MODE == MODE_STAGE2 ? 1 : 2;
-  static constexpr size_t out = LY::GW == 1 ? sizeof(E) * 2 * NKO * NC * CB : 0;
+  static constexpr size_t out = LY::GW == 1 ? sizeof(E) * NBUF * NKO * NC * CB : 0;
   // one cell per warp (n_q = 3): the volume projection is transposed through
   // shared memory, a row per Gauss point and warp holding the point's
   // contributions to 32 outputs, (F, F_t) pairs (F_t alone at stage 2); the
@@ -521,7 +527,11 @@ struct CellSmem {
   static constexpr size_t bt = TABLE ? sizeof(R) * LY::NP * CellBasis<R, ORDER, NQ>::BW : 0;
   static constexpr size_t cvt_off = raw, red_off = raw + cvt, out_off = red_off + red, tr_off = out_off + out,
                           bt_off = tr_off + tr, tab_off = bt_off + bt;
-  static constexpr size_t bytes = tab_off + tabs;
+  // GW = 1: the mbarriers of the persistent tile loop, NBUF each of full
+  // (a tile's coefficients staged), fl (a buffer's outputs written out) and
+  // done (a tile's outputs complete)
+  static constexpr size_t bar_off = (tab_off + tabs + 7) / 8 * 8;
+  static constexpr size_t bytes = bar_off + (LY::GW == 1 && DECOUPLED ? 3 * NBUF * sizeof(unsigned long long) : 0);
   static_assert(cvt_off % 16 == 0 && red_off % 16 == 0 && out_off % 16 == 0, "16-byte aligned staging");
   static_assert(tr_off % 16 == 0 && tr % 16 == 0, "16-byte aligned transpose rows");
   static_assert(bt_off % 16 == 0 && tab_off % 16 == 0, "16-byte aligned basis rows and tables");
@@ -571,6 +581,40 @@ __device__ __forceinline__ void cp_async_zfill(T* smem, const T* gmem, bool vali
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Shared-memory mbarriers (CTA scope).  mbar_wait is bounded: it gives up
+// after kMbarWaitNs of global time and returns false.
+constexpr unsigned long long kMbarWaitNs = 2000000000ull;
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(b)) : "memory");
+}
+// arrives on b once every cp.async this thread has issued so far has completed
+__device__ __forceinline__ void cp_async_mbar_arrive(unsigned long long* b) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+  const unsigned a = smem_u32(b);
+  unsigned long long t0 = 0;
+  for (int it = 0;; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    unsigned long long now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    if (it == 0)
+      t0 = now;
+    else if (now - t0 > kMbarWaitNs)
+      return false;
+  }
+}
 
 // Buffers of the cell-kernel epilogue (E: its precision, see the header).
 //   MODE 0: L, Lt (FP64, caller's)
@@ -1054,9 +1098,18 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
 
   if constexpr (GW == 1) {
     // Persistent CTAs over the tiles; the coefficients of the next tile are
-    // copied global -> shared with cp.async (double buffer) while the current
-    // tile is computed, so a CTA waits at its one barrier per tile only for
-    // the slowest of its warps, not for memory.
+    // copied global -> shared with cp.async while the current tile is
+    // computed.  Three buffers of staged coefficients and of outputs, and
+    // mbarriers in place of a CTA barrier per tile, let a warp run up to one
+    // tile ahead of the slowest warp of its CTA: in its n-th tile a thread
+    //   waits full[n]  (tile n staged),
+    //   waits done[n-2] (every warp finished tile n-2: its outputs complete,
+    //                    its coefficient buffer free), then stages tile n+1
+    //                    into that buffer and writes tile n-2's outputs out,
+    //   arrives fl[n], waits fl[n-1] (tile n-3's outputs, in the buffer that
+    //                    tile n writes, were written out by every thread),
+    //   computes tile n and arrives done[n]
+    // (buffer and barrier n mod 3; the phase of a barrier's k-th use is k & 1).
     Tin(*raw)[CB][NCP] = reinterpret_cast<Tin(*)[CB][NCP]>(smem_raw);  // [buffer][cell][v NMP + n]
     R(*cvt)[NCP] = reinterpret_cast<R(*)[NCP]>(smem_raw + S::cvt_off);  // converted copy (Tin != R)
     // tile t = (k ny + j) ntx + tx, coordinates computed once per tile in 32
@@ -1155,42 +1208,101 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         asm volatile("prefetch.global.L2 [%0];" ::"l"(pf));
       }
     };
-    unsigned t = blockIdx.x;
-    TileAt cur = at(t), prev = cur;
-    bool have_prev = false;
-    if (t < ntiles) issue(cur, 0);
-    int b = 0;
-    for (; t < ntiles; t += gridDim.x, b ^= 1) {
-      cp_async_wait_all();
-      __syncthreads();  // tile t staged by all threads; every warp is done with buffer b ^ 1
-      const unsigned tn = t + gridDim.x;
-      TileAt nxt = cur;
-      if (tn < ntiles) {
-        nxt = next_at(cur);
-        issue(nxt, b ^ 1);
-        if (MODE != MODE_STAGE2) prefetch_faces(nxt);
+    if constexpr (S::DECOUPLED) {
+      unsigned long long* const bar = reinterpret_cast<unsigned long long*>(smem_raw + S::bar_off);
+      unsigned long long *const full = bar, *const fl = bar + S::NBUF, *const done = bar + 2 * S::NBUF;
+      if (tid == 0)
+        for (int q = 0; q < 3 * S::NBUF; ++q) mbar_init(bar + q, nthr);
+      __syncthreads();  // (the tables above and the barriers' initialisation)
+      unsigned t = blockIdx.x;
+      TileAt cur = at(t), p1 = cur, p2 = cur;  // tiles n, n - 1, n - 2
+      if (t < ntiles) {
+        issue(cur, 0);
+        cp_async_mbar_arrive(&full[0]);
       }
-      if (have_prev) flush(prev, b ^ 1);
-      const R(*coef)[NCP];
-      if constexpr (std::is_same<Tin, R>::value) {
-        coef = raw[b];
-      } else {
-        // each warp converts its own cells (the only ones it reads; padding
-        // included, so that the 16-byte loads read defined values)
-        for (int e = lane; e < NCP * LY::CPW; e += 32) {
-          const int cc = warp * LY::CPW + e / NCP, c = e % NCP;
-          cvt[cc][c] = (R)raw[b][cc][c];
+      bool ok = true;
+      unsigned n = 0;
+      for (; t < ntiles; t += gridDim.x, ++n) {
+        const int x = (int)(n % 3), xm2 = (int)((n + 1) % 3), xm1 = (int)((n + 2) % 3);  // n, n - 2, n - 1 mod 3
+        ok = mbar_wait(&full[x], (n / 3) & 1);
+        if (ok && n >= 2) ok = mbar_wait(&done[xm2], ((n - 2) / 3) & 1);
+        if (!ok) break;
+        const unsigned tn = t + gridDim.x;
+        TileAt nxt = cur;
+        if (tn < ntiles) {
+          nxt = next_at(cur);
+          issue(nxt, xm2);
+          cp_async_mbar_arrive(&full[xm2]);
+          if (MODE != MODE_STAGE2) prefetch_faces(nxt);
         }
-        __syncwarp();
-        coef = cvt;
+        if (n >= 2) flush(p2, xm2);
+        mbar_arrive(&fl[x]);
+        if (n >= 1 && !(ok = mbar_wait(&fl[xm1], ((n - 1) / 3) & 1))) break;
+        const R(*coef)[NCP];
+        if constexpr (std::is_same<Tin, R>::value) {
+          coef = raw[x];
+        } else {
+          // each warp converts its own cells (the only ones it reads; padding
+          // included, so that the 16-byte loads read defined values)
+          for (int e = lane; e < NCP * LY::CPW; e += 32) {
+            const int cc = warp * LY::CPW + e / NCP, c = e % NCP;
+            cvt[cc][c] = (R)raw[x][cc][c];
+          }
+          __syncwarp();
+          coef = cvt;
+        }
+        tile(cur.i0, cur.j, cur.k, coef, so[x]);
+        mbar_arrive(&done[x]);
+        p2 = p1;
+        p1 = cur;
+        cur = nxt;
       }
-      tile(cur.i0, cur.j, cur.k, coef, so[b]);
-      prev = cur;
-      have_prev = true;
-      cur = nxt;
+      // the last two tiles' outputs
+      if (ok && n >= 2 && (ok = mbar_wait(&done[(n - 2) % 3], ((n - 2) / 3) & 1))) flush(p2, (int)((n - 2) % 3));
+      if (ok && n >= 1 && (ok = mbar_wait(&done[(n - 1) % 3], ((n - 1) / 3) & 1))) flush(p1, (int)((n - 1) % 3));
+      if (!ok) atomicOr(flag, 2u);
+      cp_async_wait_all();
+    } else {
+      // stage 2 (F_t only): two buffers and one CTA barrier per tile (the
+      // decoupled loop above ran its pass 2 % slower: the third buffers take
+      // shared memory from the L1 that serves its face-moment gathers)
+      unsigned t = blockIdx.x;
+      TileAt cur = at(t), prev = cur;
+      bool have_prev = false;
+      if (t < ntiles) issue(cur, 0);
+      int b = 0;
+      for (; t < ntiles; t += gridDim.x, b ^= 1) {
+        cp_async_wait_all();
+        __syncthreads();  // tile t staged by all threads; every warp is done with buffer b ^ 1
+        const unsigned tn = t + gridDim.x;
+        TileAt nxt = cur;
+        if (tn < ntiles) {
+          nxt = next_at(cur);
+          issue(nxt, b ^ 1);
+          if (MODE != MODE_STAGE2) prefetch_faces(nxt);
+        }
+        if (have_prev) flush(prev, b ^ 1);
+        const R(*coef)[NCP];
+        if constexpr (std::is_same<Tin, R>::value) {
+          coef = raw[b];
+        } else {
+          // each warp converts its own cells (the only ones it reads; padding
+          // included, so that the 16-byte loads read defined values)
+          for (int e = lane; e < NCP * LY::CPW; e += 32) {
+            const int cc = warp * LY::CPW + e / NCP, c = e % NCP;
+            cvt[cc][c] = (R)raw[b][cc][c];
+          }
+          __syncwarp();
+          coef = cvt;
+        }
+        tile(cur.i0, cur.j, cur.k, coef, so[b]);
+        prev = cur;
+        have_prev = true;
+        cur = nxt;
+      }
+      __syncthreads();
+      if (have_prev) flush(prev, b ^ 1);
     }
-    __syncthreads();
-    if (have_prev) flush(prev, b ^ 1);
   } else {
     R(*coef)[NCP] = reinterpret_cast<R(*)[NCP]>(smem_raw + S::cvt_off);
     const int i0 = blockIdx.x * CB, j = blockIdx.y, k = blockIdx.z;

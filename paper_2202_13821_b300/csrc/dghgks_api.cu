@@ -358,6 +358,7 @@ int read_flag(dghgks_ctx* c, cudaStream_t s) {
   if (f) {
     cudaMemsetAsync(c->flag, 0, sizeof(unsigned), s);
     cudaStreamSynchronize(s);
+    if (f & 2u) return fail(c, DGHGKS_ECUDA, "a barrier wait inside the cell kernel timed out (results invalid)");
     return fail(c, DGHGKS_EPHYS, "non-physical state (rho <= 0 or p <= 0) met at a quadrature point");
   }
   return DGHGKS_OK;

@@ -190,5 +190,6 @@ extern "C" int dghgks_residual_static(const dghgks_mesh* mesh, int order, double
   if (cudaMemcpyAsync(&flag, d->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return DGHGKS_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return DGHGKS_ECUDA;
+  if (flag & 2u) return DGHGKS_ECUDA;  // a kernel-internal barrier wait timed out
   return flag ? DGHGKS_EPHYS : DGHGKS_OK;
 }
