@@ -499,17 +499,23 @@ struct CellSmem {
   // converted copy when the input is not in the flux precision; GW > 1: one
   // buffer in the flux precision.
   // (three when DECOUPLED: a warp may run one tile ahead of the slowest warp
-  // of its CTA; two at stage 2, which keeps a CTA barrier per tile)
-  static constexpr bool DECOUPLED = MODE != MODE_STAGE2;
+  // of its CTA; two when a CTA barrier per tile orders the passes)
+#ifndef CELL_DECOUPLE_STAGE2
+#define CELL_DECOUPLE_STAGE2 0
+#endif
+  static constexpr bool DECOUPLED = MODE != MODE_STAGE2 || CELL_DECOUPLE_STAGE2;
   static constexpr int NBUF = DECOUPLED ? 3 : 2;
+  // output buffers: DECOUPLED, four (the buffer a tile writes was written out
+  // by every thread before it finished the tile two back)
+  static constexpr int NOBUF = DECOUPLED ? 4 : 2;
   static constexpr size_t raw = LY::GW == 1 ? NBUF * sizeof(Tin) * NCP * CB : 0;
   static constexpr size_t cvt = (LY::GW == 1 && std::is_same<Tin, R>::value) ? 0 : sizeof(R) * NCP * CB;
   // cross-warp partial sums (only when a cell spans two warps)
   static constexpr size_t red = LY::GW == 1 ? 0 : sizeof(R) * CB * LY::GW * 2 * LY::NOP;
   // GW = 1: the outputs of a tile (NKO kinds: two, one at stage 2; NC x CB),
-  // in NBUF buffers, so that they leave as rows of CB consecutive cells
+  // in NOBUF buffers, so that they leave as rows of CB consecutive cells
   static constexpr int NKO = MODE == MODE_STAGE2 ? 1 : 2;
-  static constexpr size_t out = LY::GW == 1 ? sizeof(E) * NBUF * NKO * NC * CB : 0;
+  static constexpr size_t out = LY::GW == 1 ? sizeof(E) * NOBUF * NKO * NC * CB : 0;
   // one cell per warp (n_q = 3): the volume projection is transposed through
   // shared memory, a row per Gauss point and warp holding the point's
   // contributions to 32 outputs, (F, F_t) pairs (F_t alone at stage 2); the
@@ -528,10 +534,9 @@ struct CellSmem {
   static constexpr size_t cvt_off = raw, red_off = raw + cvt, out_off = red_off + red, tr_off = out_off + out,
                           bt_off = tr_off + tr, tab_off = bt_off + bt;
   // GW = 1: the mbarriers of the persistent tile loop, NBUF each of full
-  // (a tile's coefficients staged), fl (a buffer's outputs written out) and
-  // done (a tile's outputs complete)
+  // (a tile's coefficients staged) and done (a tile finished by every warp)
   static constexpr size_t bar_off = (tab_off + tabs + 7) / 8 * 8;
-  static constexpr size_t bytes = bar_off + (LY::GW == 1 && DECOUPLED ? 3 * NBUF * sizeof(unsigned long long) : 0);
+  static constexpr size_t bytes = bar_off + (LY::GW == 1 && DECOUPLED ? 2 * NBUF * sizeof(unsigned long long) : 0);
   static_assert(cvt_off % 16 == 0 && red_off % 16 == 0 && out_off % 16 == 0, "16-byte aligned staging");
   static_assert(tr_off % 16 == 0 && tr % 16 == 0, "16-byte aligned transpose rows");
   static_assert(bt_off % 16 == 0 && tab_off % 16 == 0, "16-byte aligned basis rows and tables");
@@ -1099,17 +1104,19 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
   if constexpr (GW == 1) {
     // Persistent CTAs over the tiles; the coefficients of the next tile are
     // copied global -> shared with cp.async while the current tile is
-    // computed.  Three buffers of staged coefficients and of outputs, and
-    // mbarriers in place of a CTA barrier per tile, let a warp run up to one
+    // computed.  Three buffers of staged coefficients, four of outputs, and
+    // mbarriers in place of a CTA barrier per tile let a warp run up to one
     // tile ahead of the slowest warp of its CTA: in its n-th tile a thread
     //   waits full[n]  (tile n staged),
     //   waits done[n-2] (every warp finished tile n-2: its outputs complete,
-    //                    its coefficient buffer free), then stages tile n+1
-    //                    into that buffer and writes tile n-2's outputs out,
-    //   arrives fl[n], waits fl[n-1] (tile n-3's outputs, in the buffer that
-    //                    tile n writes, were written out by every thread),
-    //   computes tile n and arrives done[n]
-    // (buffer and barrier n mod 3; the phase of a barrier's k-th use is k & 1).
+    //                    its coefficient buffer free, and the outputs of tile
+    //                    n-4, which every thread wrote out before computing
+    //                    tile n-2, no longer needed), then stages tile n+1
+    //                    into that coefficient buffer and writes tile n-2's
+    //                    outputs out,
+    //   computes tile n into output buffer n mod 4 and arrives done[n]
+    // (coefficient buffers and barriers n mod 3; the phase of a barrier's
+    // k-th use is k & 1).
     Tin(*raw)[CB][NCP] = reinterpret_cast<Tin(*)[CB][NCP]>(smem_raw);  // [buffer][cell][v NMP + n]
     R(*cvt)[NCP] = reinterpret_cast<R(*)[NCP]>(smem_raw + S::cvt_off);  // converted copy (Tin != R)
     // tile t = (k ny + j) ntx + tx, coordinates computed once per tile in 32
@@ -1210,9 +1217,9 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     };
     if constexpr (S::DECOUPLED) {
       unsigned long long* const bar = reinterpret_cast<unsigned long long*>(smem_raw + S::bar_off);
-      unsigned long long *const full = bar, *const fl = bar + S::NBUF, *const done = bar + 2 * S::NBUF;
+      unsigned long long *const full = bar, *const done = bar + S::NBUF;
       if (tid == 0)
-        for (int q = 0; q < 3 * S::NBUF; ++q) mbar_init(bar + q, nthr);
+        for (int q = 0; q < 2 * S::NBUF; ++q) mbar_init(bar + q, nthr);
       __syncthreads();  // (the tables above and the barriers' initialisation)
       unsigned t = blockIdx.x;
       TileAt cur = at(t), p1 = cur, p2 = cur;  // tiles n, n - 1, n - 2
@@ -1223,7 +1230,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
       bool ok = true;
       unsigned n = 0;
       for (; t < ntiles; t += gridDim.x, ++n) {
-        const int x = (int)(n % 3), xm2 = (int)((n + 1) % 3), xm1 = (int)((n + 2) % 3);  // n, n - 2, n - 1 mod 3
+        const int x = (int)(n % 3), xm2 = (int)((n + 1) % 3);  // n, n - 2 mod 3
         ok = mbar_wait(&full[x], (n / 3) & 1);
         if (ok && n >= 2) ok = mbar_wait(&done[xm2], ((n - 2) / 3) & 1);
         if (!ok) break;
@@ -1235,9 +1242,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
           cp_async_mbar_arrive(&full[xm2]);
           if (MODE != MODE_STAGE2) prefetch_faces(nxt);
         }
-        if (n >= 2) flush(p2, xm2);
-        mbar_arrive(&fl[x]);
-        if (n >= 1 && !(ok = mbar_wait(&fl[xm1], ((n - 1) / 3) & 1))) break;
+        if (n >= 2) flush(p2, (int)((n - 2) % 4));
         const R(*coef)[NCP];
         if constexpr (std::is_same<Tin, R>::value) {
           coef = raw[x];
@@ -1251,21 +1256,20 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
           __syncwarp();
           coef = cvt;
         }
-        tile(cur.i0, cur.j, cur.k, coef, so[x]);
+        tile(cur.i0, cur.j, cur.k, coef, so[n % 4]);
         mbar_arrive(&done[x]);
         p2 = p1;
         p1 = cur;
         cur = nxt;
       }
       // the last two tiles' outputs
-      if (ok && n >= 2 && (ok = mbar_wait(&done[(n - 2) % 3], ((n - 2) / 3) & 1))) flush(p2, (int)((n - 2) % 3));
-      if (ok && n >= 1 && (ok = mbar_wait(&done[(n - 1) % 3], ((n - 1) / 3) & 1))) flush(p1, (int)((n - 1) % 3));
+      if (ok && n >= 2 && (ok = mbar_wait(&done[(n - 2) % 3], ((n - 2) / 3) & 1))) flush(p2, (int)((n - 2) % 4));
+      if (ok && n >= 1 && (ok = mbar_wait(&done[(n - 1) % 3], ((n - 1) / 3) & 1))) flush(p1, (int)((n - 1) % 4));
       if (!ok) atomicOr(flag, 2u);
       cp_async_wait_all();
     } else {
       // stage 2 (F_t only): two buffers and one CTA barrier per tile (the
-      // decoupled loop above ran its pass 2 % slower: the third buffers take
-      // shared memory from the L1 that serves its face-moment gathers)
+      // decoupled loop, CELL_DECOUPLE_STAGE2, ran this pass no faster)
       unsigned t = blockIdx.x;
       TileAt cur = at(t), prev = cur;
       bool have_prev = false;
