@@ -588,8 +588,10 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Shared-memory mbarriers (CTA scope).  mbar_wait is bounded: it gives up
-// after kMbarWaitNs of global time and returns false.
+// after kMbarWaitNs of global time, or after kMbarMaxPolls polls whatever the
+// timer says, and returns false.
 constexpr unsigned long long kMbarWaitNs = 2000000000ull;
+constexpr int kMbarMaxPolls = 1 << 24;
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
@@ -616,7 +618,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
     if (it == 0)
       t0 = now;
-    else if (now - t0 > kMbarWaitNs)
+    else if (now - t0 > kMbarWaitNs || it > kMbarMaxPolls)
       return false;
   }
 }
