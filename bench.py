@@ -678,7 +678,7 @@ def run_ours(args):
                      "roofline": roof64},
             "fp32_stage64": (None if m_s is None else
                              {"value": ranks.job_rate(dof_step, ms_s * 1e-3), "unit": UNIT, "ms_per_step": ms_s,
-                              "dtype": "f32 flux/quadrature/projection, f64 assembly + M^-1 + S2O4 combination",
+                              "dtype": "f32 flux/quadrature/projection, f64 M^-1 + S2O4 combination",
                               "roofline": roof_s}),
             "error": err, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": m32["launches"],

@@ -57,8 +57,9 @@ extern "C" {
  * M^-1 and the stage increments in FP32; the stored state, its update and
  * the reductions in FP64 */
 #define DGHGKS_FP32_MIXED 1
-/* FP32 flux, quadrature and projection sums (as DGHGKS_FP32_MIXED); the
- * assembly of a cell's volume and face contributions, M^-1 and the S2O4 stage
+/* FP32 flux, quadrature, projection sums and their assembly with the face
+ * moments (as DGHGKS_FP32_MIXED; the cell averages' face terms summed exactly,
+ * so that the conserved totals hold to FP64 rounding); M^-1 and the S2O4 stage
  * combination (Q*, the stage increment, the state update) in FP64, with the
  * stage increment stored in FP64 and Q* stored rounded to FP32 (its only
  * reader is the FP32 flux arithmetic of stage 2) */

@@ -20,7 +20,7 @@ _SO = os.path.join(_HERE, "libdghgks.so")
 
 DGHGKS_FP64 = 0
 DGHGKS_FP32_MIXED = 1
-DGHGKS_FP32_STAGE64 = 2  # FP32 flux; FP64 assembly, M^-1 and S2O4 stage combination
+DGHGKS_FP32_STAGE64 = 2  # FP32 flux and projection; FP64 M^-1 and S2O4 stage combination
 ERRORS = {-1: "bad argument", -2: "unsupported", -3: "CUDA error", -4: "non-physical state", -5: "out of memory",
           -6: "problem exceeds the fixed scratch of dghgks_residual_static"}
 

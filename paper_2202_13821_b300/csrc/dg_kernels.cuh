@@ -37,9 +37,11 @@
 //     path) stores Q* and inc in the flux precision, and the accumulation into
 //     the stored FP64 state is the one FP64 operation (on B300 an FP64
 //     instruction costs ~64 FP32 ones).  E = double with R = float (the
-//     FP32-flux / FP64-stage path): the volume sums are FP32, and the assembly with the face moments, M^-1, Q* and inc are FP64
-//     (Q* formed from the FP64 state and stored rounded to R, its precision
-//     as an input of the stage-2 flux kernels; inc stored in FP64).
+//     FP32-flux / FP64-stage path): the volume sums and their assembly with
+//     the face moments are FP32 (the mode-0 outputs' face terms summed
+//     exactly, for FP64-level conservation), M^-1, Q* and inc are FP64 (Q*
+//     formed from the FP64 state and stored rounded to R, its precision as an
+//     input of the stage-2 flux kernels; inc stored in FP64).
 //
 // Each face is computed exactly once and written by exactly one CTA, and
 // every residual coefficient is summed in a fixed order: results are
@@ -527,7 +529,7 @@ struct CellSmem {
   // per output (v, n): its offsets v NT + t_D(n) in the face blocks normal to
   // D = 0, 1, 2 and the parity signs (-1)^{n_D}; M^-1 per mode; per mode the
   // tangential indices and signs again as ints (cells spanning two warps)
-  static constexpr size_t tabs = 16 * NC + sizeof(E) * 4 * NC + sizeof(E) * NM + sizeof(int) * 6 * NM;
+  static constexpr size_t tabs = 16 * NC + sizeof(R) * 4 * NC + sizeof(E) * NM + sizeof(int) * 6 * NM;
   // the basis table (CellBasis), one row per Gauss point (persistent layout, k <= 2)
   static constexpr bool TABLE = LY::GW == 1 && ORDER <= 2;
   static constexpr size_t bt = TABLE ? sizeof(R) * LY::NP * CellBasis<R, ORDER, NQ>::BW : 0;
@@ -623,6 +625,42 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
   }
 }
 
+// Accumulators of a cell output's face terms (sg * lo - hi per face, sg = +-1):
+// PlainAcc sums in A; ExactAcc (FP32 terms) keeps the sum as an unevaluated
+// pair s + e of FP32 numbers by error-free transformations (TwoSum, Knuth,
+// TAOCP vol. 2, 4.2.2), so the FP64 value of s + e equals the exact sum to
+// within about 1e-14 relative (the rounding of the small e only).
+template <class A>
+struct PlainAcc {
+  A v;
+  __device__ __forceinline__ explicit PlainAcc(A x) : v(x) {}
+  template <class R>
+  __device__ __forceinline__ void add(R sg, R lo, R hi) {
+    v += (A)sg * (A)lo - (A)hi;
+  }
+  template <class E>
+  __device__ __forceinline__ E get() const {
+    return (E)v;
+  }
+};
+struct ExactAcc {
+  float s, e;
+  __device__ __forceinline__ explicit ExactAcc(float x) : s(x), e(0.f) {}
+  __device__ __forceinline__ void two_sum(float t) {
+    const float a = s, x = __fadd_rn(a, t), bb = __fsub_rn(x, a);
+    e = __fadd_rn(e, __fadd_rn(__fsub_rn(a, __fsub_rn(x, bb)), __fsub_rn(t, bb)));
+    s = x;
+  }
+  __device__ __forceinline__ void add(float sg, float lo, float hi) {
+    two_sum(sg * lo);  // exact: sg = +-1
+    two_sum(-hi);
+  }
+  template <class E>
+  __device__ __forceinline__ E get() const {
+    return (E)s + (E)e;
+  }
+};
+
 // Buffers of the cell-kernel epilogue (E: its precision, see the header).
 //   MODE 0: L, Lt (FP64, caller's)
 //   MODE 1: Qs = Q* in the flux precision R (the stage-2 kernels read Q* in R)
@@ -669,7 +707,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
   R* const bt = reinterpret_cast<R*>(smem_raw + S::bt_off);  // [NP][BW] basis table
   R(*red)[GW][2][NOP] = reinterpret_cast<R(*)[GW][2][NOP]>(smem_raw + S::red_off);  // GW > 1 only
   int4* dsc = reinterpret_cast<int4*>(smem_raw + S::tab_off);  // [NC] face-block offsets of output v NM + n
-  E(*dsg)[4] = reinterpret_cast<E(*)[4]>(dsc + NC);            // [NC] their parity signs
+  R(*dsg)[4] = reinterpret_cast<R(*)[4]>(dsc + NC);            // [NC] their parity signs
   E* invM = reinterpret_cast<E*>(dsg + NC);
   int* tix = reinterpret_cast<int*>(invM + NM);  // [3][NM] tangential index, then [3][NM] parity sign
   const int tid = threadIdx.x, nthr = LY::WARPS * 32;
@@ -699,10 +737,10 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
   #pragma unroll
     for (int D = 0; D < 3; ++D) {
       off[D] = v * NT + tmode_index(mode_exp(n, tan1(D)), mode_exp(n, tan2(D)));
-      dsg[e][D] = (mode_exp(n, D) % 2 == 0) ? E(1) : E(-1);
+      dsg[e][D] = (mode_exp(n, D) % 2 == 0) ? R(1) : R(-1);
     }
     dsc[e] = make_int4(off[0], off[1], off[2], n);
-    dsg[e][3] = E(0);
+    dsg[e][3] = R(0);
   }
   // basis table (persistent layout, k <= 2): one row per point
   for (int p = tid; S::TABLE && p < NP; p += nthr) {
@@ -805,48 +843,65 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     }
 
     // One output (variable v, mode n) of the cell at x index i: the six faces'
-    // moments with the sign/parity of Eq. (operator), M^-1, and the stage
-    // epilogue in the precision E; with E = R the accumulation into the
-    // stored FP64 state is the one FP64 operation.
+    // moments with the sign/parity of Eq. (operator) added to the volume sums
+    // (the assembly of R, R_t, part of the projection: in the flux precision
+    // R), then M^-1 and the stage epilogue in the precision E; with E = R the
+    // accumulation into the stored FP64 state is the one FP64 operation.
+    // SPLIT: the mode-0 outputs (the cell averages, whose totals the scheme
+    // conserves) sum their FP32 face moments exactly (ExactAcc); each face
+    // enters its two cells with opposite signs, so the totals hold to FP64
+    // rounding.
     auto finish = [&](int v, int n, int i, int cc, R sF_, R sT_) {
-      E sF = (E)sF_, sT = (E)sT_;
       const size_t cell = row + i;
       const size_t idx = (size_t)(v * NM + n) * nc + cell;
-      if constexpr (GW == 1) {
-        const int o = v * NM + n;
-        const int4 ds = dsc[o];
-        const int dof[3] = {ds.x, ds.y, ds.z};
-        E sg[3];
-        if constexpr (sizeof(E) == 4) {
-          const float4 q = *reinterpret_cast<const float4*>(dsg[o]);
-          sg[0] = q.x, sg[1] = q.y, sg[2] = q.z;
+      E sF, sT;
+      auto assemble = [&](auto aF, auto aT) {
+        if constexpr (GW == 1) {
+          const int o = v * NM + n;
+          const int4 ds = dsc[o];
+          const int dof[3] = {ds.x, ds.y, ds.z};
+          R sg[3];
+          if constexpr (sizeof(R) == 4) {
+            const float4 q = *reinterpret_cast<const float4*>(dsg[o]);
+            sg[0] = q.x, sg[1] = q.y, sg[2] = q.z;
+          } else {
+            const double2 q0 = reinterpret_cast<const double2*>(dsg[o])[0];
+            sg[0] = q0.x, sg[1] = q0.y, sg[2] = dsg[o][2];
+          }
+  #pragma unroll
+          for (int D = 0; D < 3; ++D) {
+            const R* lo = fb[D] + dof[D];
+            const R* hi = fb[3 + D] + dof[D];
+            aF.add(sg[D], lo[0], hi[0]);
+            aT.add(sg[D], lo[5 * NT], hi[5 * NT]);
+          }
         } else {
-          const double2 q0 = reinterpret_cast<const double2*>(dsg[o])[0];
-          sg[0] = q0.x, sg[1] = q0.y, sg[2] = dsg[o][2];
-        }
   #pragma unroll
-        for (int D = 0; D < 3; ++D) {
-          const R* lo = fb[D] + dof[D];
-          const R* hi = fb[3 + D] + dof[D];
-          sF += sg[D] * (E)lo[0] - (E)hi[0];
-          sT += sg[D] * (E)lo[5 * NT] - (E)hi[5 * NT];
+          for (int D = 0; D < 3; ++D) {
+            const int t = tix[D * NM + n];
+            const R sg = (R)tix[3 * NM + D * NM + n];
+            size_t up;
+            if (D == 0)
+              up = row + wrapm(i + 1, nx);
+            else if (D == 1)
+              up = ((size_t)k * ny + wrapm(j + 1, ny)) * nx + i;
+            else
+              up = ((size_t)wrapm(k + 1, nz) * ny + j) * nx + i;
+            const R* gD = G + (size_t)D * nc * (10 * NT) + v * NT + t;  // face-major: [D][face][10][NT]
+            aF.add(sg, gD[cell * (10 * NT)], gD[up * (10 * NT)]);
+            aT.add(sg, gD[cell * (10 * NT) + 5 * NT], gD[up * (10 * NT) + 5 * NT]);
+          }
         }
-      } else {
-  #pragma unroll
-      for (int D = 0; D < 3; ++D) {
-        const int t = tix[D * NM + n];
-        const E sg = (E)tix[3 * NM + D * NM + n];
-        size_t up;
-        if (D == 0)
-          up = row + wrapm(i + 1, nx);
-        else if (D == 1)
-          up = ((size_t)k * ny + wrapm(j + 1, ny)) * nx + i;
+        sF = aF.template get<E>();
+        sT = aT.template get<E>();
+      };
+      if constexpr (SPLIT) {
+        if (n == 0)
+          assemble(ExactAcc(sF_), ExactAcc(sT_));
         else
-          up = ((size_t)wrapm(k + 1, nz) * ny + j) * nx + i;
-        const R* gD = G + (size_t)D * nc * (10 * NT) + v * NT + t;  // face-major: [D][face][10][NT]
-        sF += sg * (E)gD[cell * (10 * NT)] - (E)gD[up * (10 * NT)];
-        sT += sg * (E)gD[cell * (10 * NT) + 5 * NT] - (E)gD[up * (10 * NT) + 5 * NT];
-      }
+          assemble(PlainAcc<R>(sF_), PlainAcc<R>(sT_));
+      } else {
+        assemble(PlainAcc<R>(sF_), PlainAcc<R>(sT_));
       }
       E iM = invM[n];
       if (mesh_nonuniform(m))  // 1/|K| = (2/h_x)(2/h_y)(2/h_z) / 8
