@@ -686,6 +686,12 @@ struct StageIO {
 // (two warps per cell) every pass runs 3 (cap 80, no spills): 17-21 % faster
 // than 2 at 128^3 P3; at n_q = 3 three CTAs made stage 1 slower (P3) or no
 // faster (P2).
+// CELL_PREFETCH: L2 prefetch of the next tile's face-moment blocks at stage 1
+// (with a CTA barrier per tile it saved 2 %; with the decoupled tile loop it
+// costs 0.8 %, so it is off)
+#ifndef CELL_PREFETCH
+#define CELL_PREFETCH 0
+#endif
 #ifndef CELL_MIN_CTAS_F32
 #define CELL_MIN_CTAS_F32 2
 #endif
@@ -1251,7 +1257,8 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
     // L2 prefetch of the face-moment blocks a tile's epilogue reads (its cells'
     // low faces along x, y, z and the high neighbours'), one tile ahead: they
     // were written by the face kernels long before and are no longer in L2.
-    // (Stage 2 reads only their F_t halves, and ran slower with it.)
+    // (Stage 2 reads only their F_t halves, and ran slower with it; used only
+    // when CELL_PREFETCH is set.)
     auto prefetch_faces = [&](const TileAt& a) {
       constexpr int LINES = (10 * NT * (int)sizeof(R) + 127) / 128;  // 128-byte lines per face block
       for (int e = tid; e < (5 * CB + 1) * LINES; e += nthr) {
@@ -1297,7 +1304,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
           nxt = next_at(cur);
           issue(nxt, xm2);
           cp_async_mbar_arrive(&full[xm2]);
-          if (MODE != MODE_STAGE2) prefetch_faces(nxt);
+          if (MODE != MODE_STAGE2 && CELL_PREFETCH) prefetch_faces(nxt);
         }
         if (n >= 2) flush(p2, (int)((n - 2) % 4));
         const R(*coef)[NCP];
@@ -1340,7 +1347,7 @@ __global__ void __launch_bounds__(CellLayout<ORDER, NQ>::WARPS * 32, (cell_min_c
         if (tn < ntiles) {
           nxt = next_at(cur);
           issue(nxt, b ^ 1);
-          if (MODE != MODE_STAGE2) prefetch_faces(nxt);
+          if (MODE != MODE_STAGE2 && CELL_PREFETCH) prefetch_faces(nxt);
         }
         if (have_prev) flush(prev, b ^ 1);
         const R(*coef)[NCP];
